@@ -1,0 +1,24 @@
+"""Plain FP64 CPU oracle for the Wigner-Eckart factorized collision operator.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product package imports this
+package; only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may call it.  It shares no code with the CUDA path: it has
+its own basis functions, its own real Gaunt table (computed by sphere
+quadrature, not by Wigner 3-j formulas), its own kinematic-core quadrature
+(the paper's 5D Duffy scheme with an explicit scattering-sphere rule) and a
+dense Cartesian contraction.
+
+Modules
+-------
+basis   radial Laguerre functions and real spherical harmonics (§2.2, §4.1)
+gaunt   channel list, real Gaunt tensor and its COO table (§4.1, §4.2, §4.6)
+dense   null-space / detailed-balance zeroing and the dense contraction
+        Q_a = sum_bc C_abc f_b f_c with C = R * G (§2.3, §4.1, §4.4, §4.5.1)
+core    the reduced kinematic core R by 5D singular quadrature
+        (§3.2-3.3, §4.3, Appendix A, Appendix B)
+
+Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
+``tests/test_oracle_*.py`` against closed forms or values printed in the paper
+(Table 1, Table 3, Table 5, Table 6), except the VHS (gamma=0.5) core, which the
+paper does not pin beyond conservation: "parity unpinned" for gamma not in {0, 1}.
+"""

@@ -1,0 +1,160 @@
+"""Pins of the oracle's kinematic core quadrature (§3, §4.3, §4.4, §5.2, §5.3).
+
+Each pin is fixed by something other than the oracle: closed forms (Krook-Wu
+moment system, Wang Chang-Uhlenbeck eigenvalues), values the paper prints
+(Table 3, Table 5), an exact brute-force 8D evaluation of the weak form, and
+the analytic conservation laws that the raw quadrature must already satisfy
+to rounding before the §4.4 zeroing."""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+from conftest import golden
+from oracle import basis, core, dense, gaunt
+
+
+# ----------------------------------------------------------------- Maxwell molecules
+def test_krook_wu_isotropic_maxwell():
+    """Isotropic inputs, Maxwell molecules (B = 1/4pi): with a_n = c_n N_n0 / (sqrt(4pi) n!)
+    the Fourier-transformed equation gives the closed triangular system
+    da_n/dt = sum_{j+k=n} a_j a_k j! k! / (n+1)! - a_0 a_n, exact at any truncation (§5.2.1)."""
+    km = 5
+    R = dense.conservation_zeroing(core.core(km, 0, 0.0), 0)
+    op = dense.DenseOperator(km, 0, R)
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        c = 0.2 * rng.standard_normal(km + 1)
+        c[0] = 1.0
+        N = [basis.radial_norm(n, 0) for n in range(km + 1)]
+        f = math.factorial
+        a = [c[n] * N[n] / (math.sqrt(4 * math.pi) * f(n)) for n in range(km + 1)]
+        da = [sum(a[j] * a[n - j] * f(j) * f(n - j) / f(n + 1) for j in range(n + 1)) - a[0] * a[n] for n in range(km + 1)]
+        Qex = np.array([da[n] * math.sqrt(4 * math.pi) * f(n) / N[n] for n in range(km + 1)])
+        Q = op.evaluate(c[None, :])[0]
+        assert np.allclose(Q, Qex, rtol=0, atol=1e-14)
+
+
+def _wcu_closed_form(k, l):
+    """lambda_kl = 1/2 int_{-1}^{1} [c^{2k+l} P_l(c) + s^{2k+l} P_l(s) - 1 - delta_k0 delta_l0] dx,
+    c = sqrt((1+x)/2), s = sqrt((1-x)/2): Maxwell molecules, B = 1/(4 pi), unit density."""
+    x, w = np.polynomial.legendre.leggauss(60)
+    cc, ss = np.sqrt((1 + x) / 2), np.sqrt((1 - x) / 2)
+    n = 2 * k + l
+    val = cc**n * special.eval_legendre(l, cc) + ss**n * special.eval_legendre(l, ss) - 1.0 - (1.0 if k == l == 0 else 0.0)
+    return 0.5 * np.sum(w * val)
+
+
+@pytest.fixture(scope="module")
+def maxwell_linear_blocks():
+    """Radial blocks L^{(l)}[k1, k2] of the linearized operator at c_000 = 1 (§5.3.1), Kmax=4, Lmax=6."""
+    km, lm = 4, 6
+    chans = [ch for ch in gaunt.channels(lm) if ch[1] == 0 or ch[2] == 0]
+    R = core.core(km, lm, 0.0, chans=chans)
+    g0 = 1.0 / math.sqrt(4 * math.pi)  # G[(l,m),(0,0),(l,m)]
+    blocks = {}
+    for l in range(lm + 1):
+        B = (R[chans.index((l, 0, l))][:, 0, :] + R[chans.index((l, l, 0))][:, :, 0]) * g0
+        if l == 0:
+            B[0, :] = 0.0
+            B[1, :] = 0.0
+        if l == 1:
+            B[0, :] = 0.0
+        blocks[l] = B
+    return blocks
+
+
+def test_wcu_spectrum_table3(maxwell_linear_blocks):
+    """Table 3: eigenvalues normalised by the first relaxation mode, ascending |lambda|;
+    modes 1-5 are the collision invariants (0), then -1, -1.5, -1.75, -1.8 with their degeneracies."""
+    ev = []
+    for l, B in maxwell_linear_blocks.items():
+        lam = np.linalg.eigvals(B)
+        assert np.max(np.abs(lam.imag)) < 1e-13
+        ev += list(np.repeat(lam.real, 2 * l + 1))
+    ev = np.sort(np.array(ev))[::-1]  # 0 first, then decreasing
+    assert np.all(ev < 1e-13)  # H-theorem: non-positive spectrum
+    lam6 = abs(ev[5])
+    for first, last, ratio, bound in golden("table3_wcu.txt"):
+        seg = ev[int(first) - 1:int(last)] / lam6
+        assert np.max(np.abs(seg - float(ratio))) <= max(float(bound), 1e-15) * 10
+
+
+def test_wcu_closed_form_diagonal(maxwell_linear_blocks):
+    """For Maxwell molecules the Laguerre x spherical-harmonic functions are eigenfunctions:
+    each block is diagonal with the closed-form eigenvalues lambda_kl."""
+    for l, B in maxwell_linear_blocks.items():
+        for k in range(B.shape[0]):
+            assert B[k, k] == pytest.approx(_wcu_closed_form(k, l), abs=1e-13)
+        assert np.max(np.abs(B - np.diag(np.diag(B)))) < 1e-13
+
+
+def test_bruteforce_8d_maxwell():
+    """The weak form of §2.3 evaluated directly in 8D (Gauss-Hermite in v and w, an exact
+    sphere rule for u'), exact for Maxwell molecules at small (Kmax, Lmax) because the
+    integrand is a polynomial times the Gaussian weight; compared with C = R * G of the
+    oracle core (raw, before any zeroing) entry by entry."""
+    km, lm = 1, 2
+    K, NQ = km + 1, (lm + 1) ** 2
+    N = K * NQ
+    lq = np.array([basis.lm_of_q(q)[0] for q in range(NQ)])
+    op = dense.DenseOperator(km, lm, core.core(km, lm, 0.0))
+    C_fact = np.stack([op.slice(a) for a in range(N)])
+
+    def phi(p):
+        r = np.linalg.norm(p, axis=-1)
+        Y = basis.real_sh_all(lm, p / np.maximum(r, 1e-300)[..., None])
+        Rr = basis.radial_all(K, lm, r)[..., lq]  # [..., K, NQ]
+        return (Rr * Y[..., None, :]).reshape(p.shape[:-1] + (N,))
+
+    x, w = np.polynomial.hermite_e.hermegauss(7)
+    w = w / math.sqrt(2 * math.pi)
+    grid = np.stack(np.meshgrid(x, x, x, indexing="ij"), -1).reshape(-1, 3)
+    gw = np.einsum("i,j,k->ijk", w, w, w).reshape(-1)
+    sph, sw = gaunt.sphere_rule(2 * km + lm + 1)
+    sw = sw / (4 * math.pi)  # B = 1/(4 pi)
+    phiw = phi(grid)  # phi at all w (and v) nodes
+    C = np.zeros((N, N, N))
+    for i, v in enumerate(grid):
+        V = 0.5 * (v + grid)  # [Pw, 3]
+        u = np.linalg.norm(v - grid, axis=1)
+        vp = V[:, None, :] + 0.5 * u[:, None, None] * sph[None, :, :]
+        gain = np.einsum("s,psa->pa", sw, phi(vp))
+        loss = phiw[i][None, :] * sw.sum()
+        C += gw[i] * np.einsum("p,pa,b,pc->abc", gw, gain - loss, phiw[i], phiw)
+    assert np.max(np.abs(C - C_fact)) < 1e-13 * np.max(np.abs(C))
+
+
+# ----------------------------------------------------------------- hard spheres
+def test_chapman_enskog_viscosity_table5():
+    """Table 5: f_mu = L_00 [L^{-1}]_00 of the l = 2 block for hard spheres; Kmax = 1 is 205/202."""
+    g0 = 1.0 / math.sqrt(4 * math.pi)
+    for km, ref in golden("table5_viscosity.txt"):
+        km = int(km)
+        R = core.core(km, 2, 1.0, chans=[(2, 0, 2), (2, 2, 0)])
+        B = (R[0][:, 0, :] + R[1][:, :, 0]) * g0
+        fmu = B[0, 0] * np.linalg.inv(B)[0, 0]
+        assert fmu == pytest.approx(float(ref), abs=6e-7)
+        if km == 1:
+            assert fmu == pytest.approx(205.0 / 202.0, rel=1e-13)
+
+
+def test_raw_core_conserves_before_zeroing():
+    """§4.4: the slices that the null-space correction zeroes differ from zero only by quadrature
+    error.  Checked on the raw hard-sphere core (the part symmetric in (a2, a3), which is all
+    that Q sees), together with the detailed-balance slice R^(000)_{k1,0,0}."""
+    km, lm = 3, 3
+    ch = gaunt.channels(lm)
+    idx = gaunt.channel_index(lm)
+    R = core.core(km, lm, 1.0)
+    scale = np.max(np.abs(R))
+    res = 0.0
+    for (l1, l2, l3), c in idx.items():
+        sym = R[c] + R[idx[(l1, l3, l2)]].transpose(0, 2, 1)
+        if l1 == 0:
+            res = max(res, np.max(np.abs(sym[0])), np.max(np.abs(sym[1])))
+        if l1 == 1:
+            res = max(res, np.max(np.abs(sym[0])))
+    res = max(res, np.max(np.abs(R[idx[(0, 0, 0)]][:, 0, 0])))
+    assert res < 1e-13 * scale
