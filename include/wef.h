@@ -1,0 +1,148 @@
+/*
+ * wef.h - C ABI of the GB300 Wigner-Eckart factorized Boltzmann collision operator.
+ *
+ * The library evaluates, for a batch of velocity-space cells, the bilinear
+ * Galerkin collision operator
+ *
+ *     Q_{k1,q1} = sum_c sum_{k2,k3} R^{(c)}_{k1 k2 k3} Phi^{(c,q1)}_{k2 k3},
+ *     Phi^{(c,q1)}_{k2 k3} = sum_{z in slice (c,q1)} g_z f_{k2,q2z} f_{k3,q3z}
+ *
+ * (the angular-first contraction of Sec. 4.5.4 of the paper, itself a
+ * rearrangement of the full discrete sum of Sec. 4.5 and of the dense form
+ * Q_a = sum_bc C_abc f_b f_c of Sec. 2.3 with C = R * G_R, Sec. 4.1).
+ *
+ * Basis and layout conventions (Sec. 2.2, Sec. 4.1):
+ *   K  = Kmax + 1 radial functions R_kl(v) = N_kl v^l L_k^{(l+1/2)}(v^2/2),
+ *        orthonormal under M(v) = (2 pi)^{-3/2} exp(-v^2/2) (identity mass matrix);
+ *   NQ = (Lmax+1)^2 real spherical harmonics Y_lm (no Condon-Shortley phase,
+ *        cos-type for m > 0, sin-type for m < 0), angular index q = l^2 + l + m;
+ *   one cell = K * NQ doubles, index k * NQ + q (cells contiguous: [ncells][K][NQ]).
+ *   Channels c = (l1,l2,l3) are enumerated l1 outermost, then l2, then l3
+ *   ascending, triangle rule, l1+l2+l3 even, all <= Lmax (Sec. 4.6).
+ *   The core is R[c][k1][k2][k3] (FP64), c in that order.
+ *   The real Gaunt weight of a COO row is g = integral over S^2 of
+ *   Y_q1 Y_q2 Y_q3 (Table 1 prints these values).
+ *
+ * Ownership: the caller owns every pointer it passes; the library copies what
+ * it keeps (tables and the uploaded core live on the device until
+ * wef_destroy).  Device pointers are plain CUDA device addresses; host
+ * pointers are plain host addresses.
+ *
+ * Errors: every call returns a wef_status; on failure wef_last_error() gives a
+ * thread-local message.  No call throws across the ABI.  NaN/Inf in the inputs
+ * propagate to the outputs and are not checked.
+ */
+#ifndef WEF_H
+#define WEF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wef_operator* wef_op;
+
+typedef enum {
+  WEF_OK = 0,
+  WEF_EINVAL = -1,  /* bad argument (null pointer, size out of range, misaligned buffer) */
+  WEF_ENOMEM = -2,  /* device or host allocation failed */
+  WEF_ECUDA = -3,   /* a CUDA runtime call failed (message has the CUDA error string) */
+  WEF_ENOCORE = -4, /* evaluate called before wef_upload_core */
+  WEF_ESHAPE = -5,  /* (Kmax, Lmax) outside the supported range or mismatched lengths */
+  WEF_ETIMEOUT = -6 /* a bounded device-side wait gave up (status word set by a kernel) */
+} wef_status;
+
+typedef enum {
+  WEF_FP64 = 0,       /* everything in FP64 (angular coupling and radial contraction) */
+  WEF_MIXED_BF16 = 1, /* FP64 angular coupling, BF16 x BF16 -> FP32 radial stage on tcgen05 */
+  WEF_MIXED_TF32 = 2  /* FP64 angular coupling, TF32 x TF32 -> FP32 radial stage on tcgen05 */
+} wef_precision;
+
+/* Flags of wef_upload_core. */
+#define WEF_CORE_APPLY_NULLSPACE 1u /* zero the Sec. 4.4.2/4.4.3 slices of R before use */
+
+/* Supported sizes: 0 <= Kmax <= 16, 0 <= Lmax <= 20. */
+#define WEF_MAX_KMAX 16
+#define WEF_MAX_LMAX 20
+
+/*
+ * wef_create - build the angular geometry of a (Kmax, Lmax) operator.
+ * Sec. 4.1-4.2: channel list, real Gaunt table (exact Wigner 3-j values turned
+ * real by the unitary complex->real map), slices (c, q1), and the device
+ * programs of the evaluation kernels.  gamma is the cross-section exponent of
+ * B = u^gamma / (4 pi) (0 Maxwell molecules, 1 hard spheres, 0.5 VHS); it is
+ * only recorded here (the core carries the physics).  Uses the current CUDA
+ * device.  On success *out owns device memory until wef_destroy.
+ */
+wef_status wef_create(int kmax, int lmax, double gamma, wef_op* out);
+
+/* Sizes of the operator: N = K*NQ per cell, number of channels N_T, Gaunt
+ * nonzeros N_G, and the core length N_T*K^3 (doubles).  Any out pointer may be NULL. */
+wef_status wef_sizes(wef_op op, int64_t* n_per_cell, int64_t* n_channels, int64_t* n_gaunt, int64_t* core_len);
+
+/* Copy the COO table of Table 1 order (q3 slowest, q1 fastest; 0-based
+ * indices) into host arrays of length >= N_G.  Any array may be NULL. */
+wef_status wef_gaunt_coo(wef_op op, int32_t* q1, int32_t* q2, int32_t* q3, int32_t* c, double* g);
+
+/*
+ * wef_upload_core - copy a core R[c][k1][k2][k3] (FP64 host array of length
+ * N_T*K^3) to the device and derive the per-precision operand tables.  With
+ * WEF_CORE_APPLY_NULLSPACE, the mass/momentum/energy slices (Sec. 4.4.2) and the
+ * detailed-balance slice R^{(000)}_{k1,0,0} (Sec. 4.4.3) are zeroed first.
+ * Synchronous.  The caller keeps R_host.  May be called again to replace the core.
+ */
+wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigned flags);
+
+/* Bytes of device workspace wef_evaluate needs for ncells cells (256-byte aligned use). */
+wef_status wef_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int64_t* bytes);
+
+/*
+ * wef_evaluate - Q = Q(f, f) for ncells cells on `stream` (asynchronous).
+ * f_dev, q_dev: device arrays [ncells][K][NQ] FP64 (may not alias).
+ * workspace: device buffer of at least wef_workspace_size bytes, 256-byte aligned;
+ * it is scratch (overwritten), and calls that share it must be ordered on the GPU.
+ * stream: a cudaStream_t (NULL = legacy default stream).  Allocates nothing.
+ * The conservation projection (Sec. 4.4) writes exact zeros to the mass,
+ * momentum and energy outputs (k=0,l=0), (k=0,l=1), (k=1,l=0) of every cell.
+ * ncells == 0 is a no-op.
+ */
+wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t ncells, wef_precision prec,
+                        void* workspace, int64_t workspace_bytes, void* stream);
+
+/*
+ * wef_core_build - the kinematic core R[c][k1][k2][k3] of the operator by the
+ * singular quadrature of Sec. 4.3 / Appendix A-B, on the host (all cores of the
+ * machine).  pad_rad / pad_ang are the selective paddings of Appendix B (the
+ * paper uses 10-20).  R_out: host array of length N_T*K^3.  Raw core: no
+ * conservation zeroing is applied (pass WEF_CORE_APPLY_NULLSPACE to upload).
+ */
+wef_status wef_core_build(wef_op op, int pad_rad, int pad_ang, double* R_out, int64_t len);
+
+/*
+ * wef_flops - arithmetic the evaluation executes per cell: FP64 flops (angular
+ * coupling, plus the radial contraction for WEF_FP64) and tensor-core flops
+ * (radial contraction, padded MMA shapes, for the mixed precisions).  An FMA
+ * counts as 2.  Derived from the operator's programs; any out pointer may be NULL.
+ */
+wef_status wef_flops(wef_op op, wef_precision prec, double* fp64_flops_per_cell, double* tc_flops_per_cell);
+
+/*
+ * wef_set_trace_events - tracing hook: when ev_start/ev_stop (cudaEvent_t) are
+ * non-NULL, the next wef_evaluate calls record ev_start on the stream just before
+ * the dominant (contraction) kernel and ev_stop just after it, so callers can
+ * time that kernel alone.  Pass NULLs to switch tracing off.
+ */
+wef_status wef_set_trace_events(wef_op op, void* ev_start, void* ev_stop);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* wef_last_error(void);
+
+/* Release the operator and its device memory.  NULL is accepted. */
+wef_status wef_destroy(wef_op op);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WEF_H */

@@ -1,0 +1,177 @@
+"""Python binding of libwef (the C ABI in include/wef.h): argument marshalling only.
+
+Every computation runs in the library: the evaluation in its sm_103a kernels,
+table and core construction in its host code.  The functions below carry the
+C names; ``Operator`` is a small convenience wrapper that takes torch tensors
+(PyTorch is used only for device memory and streams).  If the shared library
+is missing the import of any function fails loudly; there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwef.so")
+
+WEF_OK, WEF_EINVAL, WEF_ENOMEM, WEF_ECUDA, WEF_ENOCORE, WEF_ESHAPE, WEF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+WEF_FP64, WEF_MIXED_BF16, WEF_MIXED_TF32 = 0, 1, 2
+WEF_CORE_APPLY_NULLSPACE = 1
+PRECISIONS = {"fp64": WEF_FP64, "bf16": WEF_MIXED_BF16, "tf32": WEF_MIXED_TF32}
+
+_lib = None
+
+
+class WefError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"wef status {status}: {msg}")
+        self.status = status
+
+
+def lib():
+    """The loaded shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python {os.path.join(_HERE, 'build.py')}`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32p, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "wef_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(vp)], ctypes.c_int),
+            "wef_sizes": ([vp, i64p, i64p, i64p, i64p], ctypes.c_int),
+            "wef_gaunt_coo": ([vp, i32p, i32p, i32p, i32p, dp], ctypes.c_int),
+            "wef_upload_core": ([vp, dp, i64, ctypes.c_uint], ctypes.c_int),
+            "wef_workspace_size": ([vp, i64, ctypes.c_int, i64p], ctypes.c_int),
+            "wef_evaluate": ([vp, vp, vp, i64, ctypes.c_int, vp, i64, vp], ctypes.c_int),
+            "wef_core_build": ([vp, ctypes.c_int, ctypes.c_int, dp, i64], ctypes.c_int),
+            "wef_flops": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
+            "wef_set_trace_events": ([vp, vp, vp], ctypes.c_int),
+            "wef_last_error": ([], ctypes.c_char_p),
+            "wef_destroy": ([vp], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != WEF_OK:
+        raise WefError(status, lib().wef_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def wef_create(kmax, lmax, gamma):
+    h = ctypes.c_void_p()
+    _check(lib().wef_create(int(kmax), int(lmax), float(gamma), ctypes.byref(h)))
+    return h
+
+
+def wef_sizes(op):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().wef_sizes(op, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def wef_gaunt_coo(op):
+    n = wef_sizes(op)[2]
+    q1, q2, q3, c = (np.empty(n, np.int32) for _ in range(4))
+    g = np.empty(n, np.float64)
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))  # noqa: E731
+    _check(lib().wef_gaunt_coo(op, ip(q1), ip(q2), ip(q3), ip(c), _dp(g)))
+    return q1, q2, q3, c, g
+
+
+def wef_upload_core(op, R, flags=WEF_CORE_APPLY_NULLSPACE):
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    _check(lib().wef_upload_core(op, _dp(R), R.size, int(flags)))
+
+
+def wef_workspace_size(op, ncells, prec=WEF_FP64):
+    b = ctypes.c_int64()
+    _check(lib().wef_workspace_size(op, int(ncells), int(prec), ctypes.byref(b)))
+    return b.value
+
+
+def wef_evaluate(op, f_ptr, q_ptr, ncells, prec, ws_ptr, ws_bytes, stream_ptr):
+    _check(lib().wef_evaluate(op, f_ptr, q_ptr, int(ncells), int(prec), ws_ptr, int(ws_bytes), stream_ptr))
+
+
+def wef_core_build(op, pad_rad=20, pad_ang=20):
+    n = wef_sizes(op)[3]
+    R = np.empty(n, np.float64)
+    _check(lib().wef_core_build(op, int(pad_rad), int(pad_ang), _dp(R), n))
+    return R
+
+
+def wef_flops(op, prec=WEF_FP64):
+    a, t = ctypes.c_double(), ctypes.c_double()
+    _check(lib().wef_flops(op, int(prec), ctypes.byref(a), ctypes.byref(t)))
+    return a.value, t.value
+
+
+def wef_set_trace_events(op, ev_start, ev_stop):
+    _check(lib().wef_set_trace_events(op, ev_start, ev_stop))
+
+
+def wef_last_error():
+    return lib().wef_last_error().decode()
+
+
+def wef_destroy(op):
+    _check(lib().wef_destroy(op))
+
+
+class Operator:
+    """Owns a wef_op; evaluates Q(f, f) on torch CUDA tensors [ncells, K, NQ] float64."""
+
+    def __init__(self, kmax, lmax, gamma):
+        self.kmax, self.lmax, self.gamma = kmax, lmax, gamma
+        self.K, self.NQ = kmax + 1, (lmax + 1) ** 2
+        self.h = wef_create(kmax, lmax, gamma)
+        self.N, self.n_channels, self.n_gaunt, self.core_len = wef_sizes(self.h)
+        self._ws = None
+
+    def build_core(self, pad_rad=20, pad_ang=20):
+        return wef_core_build(self.h, pad_rad, pad_ang).reshape(self.n_channels, self.K, self.K, self.K)
+
+    def upload_core(self, R, flags=WEF_CORE_APPLY_NULLSPACE):
+        wef_upload_core(self.h, R, flags)
+
+    def workspace(self, ncells, prec, device):
+        import torch
+
+        need = wef_workspace_size(self.h, ncells, prec)
+        if self._ws is None or self._ws.numel() < max(need, 256) or self._ws.device != device:
+            self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=device)
+        return self._ws
+
+    def evaluate(self, f, q=None, precision="fp64", stream=None):
+        import torch
+
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        assert f.is_cuda and f.dtype == torch.float64 and f.is_contiguous()
+        ncells = f.shape[0]
+        if q is None:
+            q = torch.empty_like(f)
+        ws = self.workspace(ncells, prec, f.device)
+        st = stream if stream is not None else torch.cuda.current_stream(f.device)
+        wef_evaluate(self.h, f.data_ptr(), q.data_ptr(), ncells, prec, ws.data_ptr(), ws.numel(), st.cuda_stream)
+        return q
+
+    def close(self):
+        if self.h is not None:
+            wef_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

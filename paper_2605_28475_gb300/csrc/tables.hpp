@@ -1,0 +1,66 @@
+// Host-side angular geometry of the operator (paper Sec. 4.1, 4.2, 4.5.4, 4.6).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace wef {
+
+struct Channel {
+  int l1, l2, l3;
+};
+
+// Wigner 3-j symbol (j1 j2 j3; m1 m2 m3) for integer arguments, exact integer
+// binomial sum times a prime-factorised square-root prefactor.
+double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3);
+
+// Real Gaunt coefficient: integral over S^2 of Y_{l1 m1} Y_{l2 m2} Y_{l3 m3}
+// for the real harmonics of the library (no Condon-Shortley phase, cos-type for
+// m > 0, sin-type for m < 0), from complex Gaunt coefficients mapped by the
+// unitary complex -> real transform (Sec. 4.1).
+double real_gaunt(int l1, int m1, int l2, int m2, int l3, int m3);
+
+// One evaluation "program": the instruction stream that the kernels walk.
+// Tasks are groups of output rows (cell x q1); each task lists its channels,
+// and per channel and per q1 slot the rank-1 groups (q2; entries (q3, w)).
+//
+// Layout of prog (int32 words), per task:
+//   [q1_base, nslots, nchan]
+//   per channel: [sc, ngroups_slot0, ..., ngroups_slot{nslots-1}]
+//     per slot, per group: [q2 | ne << 16], then ne words q3
+// Weights are consumed in stream order from progw, starting at task_w[t].
+struct Program {
+  int nslots = 1;
+  std::vector<int32_t> prog;
+  std::vector<double> progw;
+  std::vector<int32_t> task_off;  // word offset of task t (size ntasks + 1)
+  std::vector<int32_t> task_w;    // weight offset of task t
+  std::vector<double> task_cost;  // FP64 flops per cell of task t (for load balance)
+  std::vector<int32_t> task_l1;
+  int ntasks() const { return (int)task_cost.size(); }
+};
+
+struct Tables {
+  int kmax = 0, lmax = 0, K = 0, NQ = 0;
+  std::vector<Channel> chans;        // paper order
+  std::vector<int> chan_of;          // (l1*(L+1)+l2)*(L+1)+l3 -> c, or -1
+  std::vector<int32_t> q1, q2, q3, c;  // COO, Table 1 order (q3 slowest, q1 fastest)
+  std::vector<double> g;
+  // symmetrised channel set used by the kernels: channels with l2 <= l3;
+  // sym_partner[s] is the paper index of (l1, l3, l2)
+  std::vector<int> sym_chan, sym_partner;
+  Program prog1;  // one q1 per task (FP64 path)
+  Program prog4;  // up to four q1 of one shell per task (tensor-core path, 128-row tiles)
+  int64_t n_sym_entries = 0, n_sym_groups = 0, n_sym_slices = 0;
+};
+
+// Build everything; returns "" on success or an error message.
+std::string build_tables(int kmax, int lmax, Tables& t);
+
+inline int lq(int q) {
+  int l = 0;
+  while ((l + 1) * (l + 1) <= q) ++l;
+  return l;
+}
+
+}  // namespace wef

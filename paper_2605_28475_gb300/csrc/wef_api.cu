@@ -1,0 +1,295 @@
+// C ABI of the library (declared in include/wef.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/wef.h"
+#include "wef_internal.hpp"
+
+using namespace wef;
+
+namespace {
+
+thread_local std::string g_err;
+
+wef_status fail(wef_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+wef_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(WEF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  *dst = nullptr;
+  if (src.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)dst, src.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Split tasks [0, ntasks) into n contiguous chunks of about equal cost.
+std::vector<int32_t> split_tasks(const std::vector<double>& cost, int n) {
+  const int nt = (int)cost.size();
+  n = std::max(1, std::min(n, nt));
+  double total = 0.0;
+  for (double c : cost) total += c;
+  std::vector<int32_t> b(1, 0);
+  double acc = 0.0;
+  int t = 0;
+  for (int i = 1; i < n; ++i) {
+    const double target = total * i / n;
+    while (t < nt && acc + 0.5 * cost[t] < target) acc += cost[t++];
+    if (t <= b.back()) t = b.back() + 1;
+    if (t > nt - (n - i)) t = nt - (n - i);
+    b.push_back(t);
+  }
+  b.push_back(nt);
+  return b;
+}
+
+}  // namespace
+
+struct wef_operator {
+  Tables T;
+  double gamma = 0.0;
+  int device = 0;
+  int sms = 1;
+  // programs
+  int32_t *d_prog1 = nullptr, *d_off1 = nullptr, *d_w1 = nullptr;
+  double* d_progw1 = nullptr;
+  // chunk bounds for the FP64 path, one set per power-of-two chunk count
+  std::vector<int> chunk_n;    // chunk counts available
+  std::vector<int> chunk_pos;  // offset of each set in d_chunks1
+  int32_t* d_chunks1 = nullptr;
+  // core
+  double* d_R64 = nullptr;  // symmetrised core [sc][k3][k1][k2]
+  bool has_core = false;
+  // tracing
+  cudaEvent_t trace_start = nullptr, trace_stop = nullptr;
+
+  void release() {
+    cudaFree(d_prog1);
+    cudaFree(d_off1);
+    cudaFree(d_w1);
+    cudaFree(d_progw1);
+    cudaFree(d_chunks1);
+    cudaFree(d_R64);
+    d_prog1 = d_off1 = d_w1 = d_chunks1 = nullptr;
+    d_progw1 = d_R64 = nullptr;
+  }
+};
+
+namespace {
+
+// Device-side set-up (programs, chunk tables) on the current device; done at the
+// first call that needs the GPU so that host-only use (tables, core building)
+// works on machines without one.
+cudaError_t ensure_device(wef_operator* op) {
+  if (op->d_prog1) return cudaSuccess;
+  cudaError_t e = cudaGetDevice(&op->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&op->sms, cudaDevAttrMultiProcessorCount, op->device);
+  const Program& P = op->T.prog1;
+  if (e == cudaSuccess) e = upload(&op->d_prog1, P.prog);
+  if (e == cudaSuccess) e = upload(&op->d_progw1, P.progw);
+  if (e == cudaSuccess) e = upload(&op->d_off1, P.task_off);
+  if (e == cudaSuccess) e = upload(&op->d_w1, P.task_w);
+  if (e == cudaSuccess) {
+    std::vector<int32_t> all;
+    op->chunk_n.clear();
+    op->chunk_pos.clear();
+    for (int n = 1; n <= P.ntasks(); n *= 2) {
+      std::vector<int32_t> b = split_tasks(P.task_cost, n);
+      op->chunk_n.push_back((int)b.size() - 1);
+      op->chunk_pos.push_back((int)all.size());
+      all.insert(all.end(), b.begin(), b.end());
+    }
+    e = upload(&op->d_chunks1, all);
+  }
+  if (e != cudaSuccess) op->release();
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* wef_last_error(void) { return g_err.c_str(); }
+
+wef_status wef_create(int kmax, int lmax, double gamma, wef_op* out) {
+  if (!out) return fail(WEF_EINVAL, "wef_create: out is NULL");
+  *out = nullptr;
+  if (kmax < 0 || kmax > WEF_MAX_KMAX || lmax < 0 || lmax > WEF_MAX_LMAX)
+    return fail(WEF_ESHAPE, "wef_create: Kmax must be in [0,16] and Lmax in [0,20]");
+  if (!(gamma >= 0.0 && gamma <= 2.0)) return fail(WEF_EINVAL, "wef_create: gamma must be in [0, 2]");
+  wef_operator* op = new (std::nothrow) wef_operator();
+  if (!op) return fail(WEF_ENOMEM, "wef_create: host allocation failed");
+  op->gamma = gamma;
+  std::string err = build_tables(kmax, lmax, op->T);
+  if (!err.empty()) {
+    delete op;
+    return fail(WEF_ESHAPE, "wef_create: " + err);
+  }
+  *out = op;
+  return WEF_OK;
+}
+
+wef_status wef_sizes(wef_op op, int64_t* n_per_cell, int64_t* n_channels, int64_t* n_gaunt, int64_t* core_len) {
+  if (!op) return fail(WEF_EINVAL, "wef_sizes: op is NULL");
+  const int64_t K = op->T.K;
+  if (n_per_cell) *n_per_cell = K * op->T.NQ;
+  if (n_channels) *n_channels = (int64_t)op->T.chans.size();
+  if (n_gaunt) *n_gaunt = (int64_t)op->T.g.size();
+  if (core_len) *core_len = (int64_t)op->T.chans.size() * K * K * K;
+  return WEF_OK;
+}
+
+wef_status wef_gaunt_coo(wef_op op, int32_t* q1, int32_t* q2, int32_t* q3, int32_t* c, double* g) {
+  if (!op) return fail(WEF_EINVAL, "wef_gaunt_coo: op is NULL");
+  const size_t n = op->T.g.size();
+  if (q1) std::memcpy(q1, op->T.q1.data(), n * sizeof(int32_t));
+  if (q2) std::memcpy(q2, op->T.q2.data(), n * sizeof(int32_t));
+  if (q3) std::memcpy(q3, op->T.q3.data(), n * sizeof(int32_t));
+  if (c) std::memcpy(c, op->T.c.data(), n * sizeof(int32_t));
+  if (g) std::memcpy(g, op->T.g.data(), n * sizeof(double));
+  return WEF_OK;
+}
+
+wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigned flags) {
+  if (!op || !R_host) return fail(WEF_EINVAL, "wef_upload_core: NULL argument");
+  const Tables& T = op->T;
+  const int K = T.K;
+  const int64_t K3 = (int64_t)K * K * K;
+  const int64_t NT = (int64_t)T.chans.size();
+  if (len != NT * K3) return fail(WEF_ESHAPE, "wef_upload_core: len must be N_T*K^3");
+  cudaError_t de = ensure_device(op);
+  if (de != cudaSuccess) return cuda_fail(de, "wef_upload_core: device set-up");
+  std::vector<double> R(R_host, R_host + len);
+  if (flags & WEF_CORE_APPLY_NULLSPACE) {
+    for (int64_t c = 0; c < NT; ++c) {
+      const Channel& h = T.chans[c];
+      double* Rc = &R[c * K3];
+      if (h.l1 == 0) {
+        std::fill(Rc, Rc + K * K, 0.0);                              // mass, k1 = 0
+        if (K > 1) std::fill(Rc + K * K, Rc + 2 * K * K, 0.0);       // energy, k1 = 1
+      }
+      if (h.l1 == 1) std::fill(Rc, Rc + K * K, 0.0);                 // momentum, k1 = 0
+      if (h.l1 == 0 && h.l2 == 0 && h.l3 == 0)
+        for (int k1 = 0; k1 < K; ++k1) Rc[(int64_t)k1 * K * K] = 0.0;  // detailed balance
+    }
+  }
+  // symmetrised core Rt[sc] = R[c] + R[c']^{T23}, FP64 layout [sc][k3][k1][k2]
+  const int NS = (int)T.sym_chan.size();
+  std::vector<double> R64((size_t)NS * K3);
+  for (int s = 0; s < NS; ++s) {
+    const double* A = &R[(int64_t)T.sym_chan[s] * K3];
+    const double* B = &R[(int64_t)T.sym_partner[s] * K3];
+    for (int k1 = 0; k1 < K; ++k1)
+      for (int k2 = 0; k2 < K; ++k2)
+        for (int k3 = 0; k3 < K; ++k3) {
+          const double v = A[(k1 * K + k2) * K + k3] + B[(k1 * K + k3) * K + k2];
+          R64[(((size_t)s * K + k3) * K + k1) * K + k2] = v;
+        }
+  }
+  cudaFree(op->d_R64);
+  op->d_R64 = nullptr;
+  op->has_core = false;
+  cudaError_t e = upload(&op->d_R64, R64);
+  if (e != cudaSuccess) return cuda_fail(e, "wef_upload_core");
+  op->has_core = true;
+  return WEF_OK;
+}
+
+wef_status wef_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int64_t* bytes) {
+  if (!op || !bytes || ncells < 0) return fail(WEF_EINVAL, "wef_workspace_size: bad argument");
+  (void)prec;
+  const int64_t ntiles = (ncells + 31) / 32;
+  *bytes = ntiles * 32 * (int64_t)op->T.K * op->T.NQ * (int64_t)sizeof(double);
+  return WEF_OK;
+}
+
+wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t ncells, wef_precision prec,
+                        void* workspace, int64_t workspace_bytes, void* stream) {
+  if (!op) return fail(WEF_EINVAL, "wef_evaluate: op is NULL");
+  if (ncells < 0) return fail(WEF_EINVAL, "wef_evaluate: ncells < 0");
+  if (ncells == 0) return WEF_OK;
+  if (!f_dev || !q_dev || !workspace) return fail(WEF_EINVAL, "wef_evaluate: NULL buffer");
+  if (!op->has_core) return fail(WEF_ENOCORE, "wef_evaluate: no core uploaded");
+  if (((uintptr_t)workspace & 255) != 0) return fail(WEF_EINVAL, "wef_evaluate: workspace not 256-byte aligned");
+  int64_t need = 0;
+  wef_workspace_size(op, ncells, prec, &need);
+  if (workspace_bytes < need) return fail(WEF_EINVAL, "wef_evaluate: workspace too small");
+  if (ncells > (int64_t)65535 * 32 * 1024) return fail(WEF_EINVAL, "wef_evaluate: ncells too large");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = op->T.K, NQ = op->T.NQ;
+  double* ftile = (double*)workspace;
+  cudaError_t e = launch_tile_f(f_dev, ftile, ncells, K, NQ, s);
+  if (e != cudaSuccess) return cuda_fail(e, "wef_evaluate: tile kernel");
+  if (prec != WEF_FP64) return fail(WEF_EINVAL, "wef_evaluate: precision not available");
+  // chunk count: enough CTAs for several waves of the GPU
+  const int64_t ntiles = (ncells + 31) / 32;
+  const int64_t want = 4LL * op->sms;
+  int idx = 0;
+  while (idx + 1 < (int)op->chunk_n.size() && ntiles * op->chunk_n[idx] < want) ++idx;
+  DevProgram p{op->d_prog1, op->d_progw1, op->d_off1, op->d_w1, op->T.prog1.ntasks()};
+  if (op->trace_start) cudaEventRecord(op->trace_start, s);
+  e = launch_fp64(K, ftile, q_dev, ncells, NQ, p, op->d_chunks1 + op->chunk_pos[idx], op->chunk_n[idx], op->d_R64, s);
+  if (op->trace_stop) cudaEventRecord(op->trace_stop, s);
+  if (e != cudaSuccess) return cuda_fail(e, "wef_evaluate: fp64 kernel");
+  return WEF_OK;
+}
+
+wef_status wef_core_build(wef_op op, int pad_rad, int pad_ang, double* R_out, int64_t len) {
+  if (!op || !R_out) return fail(WEF_EINVAL, "wef_core_build: NULL argument");
+  const int64_t K = op->T.K;
+  if (len != (int64_t)op->T.chans.size() * K * K * K) return fail(WEF_ESHAPE, "wef_core_build: len must be N_T*K^3");
+  if (pad_rad < 0 || pad_ang < 0 || pad_rad > 200 || pad_ang > 200) return fail(WEF_EINVAL, "wef_core_build: bad padding");
+  std::string err = core_build(op->T, op->gamma, pad_rad, pad_ang, R_out);
+  if (!err.empty()) return fail(WEF_EINVAL, "wef_core_build: " + err);
+  return WEF_OK;
+}
+
+wef_status wef_flops(wef_op op, wef_precision prec, double* fp64_flops_per_cell, double* tc_flops_per_cell) {
+  if (!op) return fail(WEF_EINVAL, "wef_flops: op is NULL");
+  const Program& P = prec == WEF_FP64 ? op->T.prog1 : op->T.prog4;
+  double f64 = 0.0;
+  for (double c : P.task_cost) f64 += c;
+  double tc = 0.0;
+  if (prec != WEF_FP64) {
+    // radial stage on the tensor cores: per task and channel, a 128-row tile times
+    // the padded K^2 x N operand; per cell that is (128/32) rows per task and channel
+    const int K = op->T.K;
+    const int kpad = prec == WEF_MIXED_BF16 ? (K * K + 15) / 16 * 16 : (K * K + 7) / 8 * 8;
+    const int npad = (K + 15) / 16 * 16;
+    for (int t = 0; t < P.ntasks(); ++t) {
+      const int nchan = P.prog[P.task_off[t] + 2];
+      tc += 2.0 * 4.0 * kpad * npad * nchan;
+    }
+  }
+  if (fp64_flops_per_cell) *fp64_flops_per_cell = f64;
+  if (tc_flops_per_cell) *tc_flops_per_cell = tc;
+  return WEF_OK;
+}
+
+wef_status wef_set_trace_events(wef_op op, void* ev_start, void* ev_stop) {
+  if (!op) return fail(WEF_EINVAL, "wef_set_trace_events: op is NULL");
+  op->trace_start = (cudaEvent_t)ev_start;
+  op->trace_stop = (cudaEvent_t)ev_stop;
+  return WEF_OK;
+}
+
+wef_status wef_destroy(wef_op op) {
+  if (!op) return WEF_OK;
+  op->release();
+  delete op;
+  return WEF_OK;
+}
+
+}  // extern "C"

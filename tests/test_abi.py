@@ -1,0 +1,90 @@
+"""The C ABI: the library loads, exports every symbol include/wef.h declares, and its
+host-side parts (angular tables, core quadrature, argument checks) agree with the
+oracle.  No GPU compute here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2605_28475_gb300 as W
+from oracle import core as ocore
+from oracle import gaunt as ogaunt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:wef_status|const char\*)\s+(wef_\w+)\s*\(", src, re.M))
+    return names
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not os.path.exists(W.LIB_PATH):
+        from paper_2605_28475_gb300 import build
+
+        build.build()
+
+
+def test_exports_every_declared_symbol():
+    names = _declared_symbols()
+    assert {"wef_create", "wef_evaluate", "wef_upload_core", "wef_destroy"} <= names
+    lib = W.lib()
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("L", [2, 4, 8, 12])
+def test_gaunt_table_matches_oracle(L):
+    """Exact 3-j route (library) vs sphere quadrature (oracle): same rows, same order, same weights."""
+    h = W.wef_create(1, L, 0.0)
+    try:
+        q1, q2, q3, c, g = W.wef_gaunt_coo(h)
+        o = ogaunt.coo(L)
+        for a, b in zip((q1, q2, q3, c), o[:4]):
+            assert np.array_equal(a, b)
+        assert np.max(np.abs(g - o[4])) < 1e-13
+        nq, nt, ng, rl = W.wef_sizes(h)
+        assert (nq, nt, ng, rl) == (2 * (L + 1) ** 2, len(ogaunt.channels(L)), len(g), len(ogaunt.channels(L)) * 8)
+    finally:
+        W.wef_destroy(h)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.5, 1.0])
+def test_core_builder_matches_oracle_core(gamma):
+    """The library's core quadrature (Funk-Hecke sphere means, C++) against the oracle's
+    (explicit scattering-sphere rule, numpy): two independent evaluations of the same integral."""
+    km, lm = 2, 3
+    h = W.wef_create(km, lm, gamma)
+    try:
+        Rp = W.wef_core_build(h).reshape(-1, km + 1, km + 1, km + 1)
+    finally:
+        W.wef_destroy(h)
+    Ro = ocore.core(km, lm, gamma)
+    assert np.max(np.abs(Rp - Ro)) < 1e-13 * np.max(np.abs(Ro))
+
+
+def test_argument_errors():
+    with pytest.raises(W.WefError) as e:
+        W.wef_create(17, 4, 0.0)
+    assert e.value.status == W.WEF_ESHAPE
+    with pytest.raises(W.WefError):
+        W.wef_create(4, 21, 0.0)
+    with pytest.raises(W.WefError):
+        W.wef_create(4, 4, -1.0)
+    h = W.wef_create(2, 2, 0.0)
+    try:
+        with pytest.raises(W.WefError) as e:
+            W.wef_upload_core(h, np.zeros(5))
+        assert e.value.status == W.WEF_ESHAPE
+        with pytest.raises(W.WefError):
+            W.wef_workspace_size(h, -1)
+        assert W.wef_workspace_size(h, 0) == 0
+        assert W.wef_workspace_size(h, 33) == 64 * 3 * 9 * 8
+    finally:
+        W.wef_destroy(h)
