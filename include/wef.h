@@ -135,6 +135,15 @@ wef_status wef_flops(wef_op op, wef_precision prec, double* fp64_flops_per_cell,
  */
 wef_status wef_set_trace_events(wef_op op, void* ev_start, void* ev_stop);
 
+/*
+ * wef_device_status - synchronous check of the operator's device status word:
+ * WEF_ETIMEOUT if any earlier evaluation had a bounded in-kernel wait (mbarrier
+ * on a tensor-core or bulk-copy completion) give up, in which case that
+ * evaluation's outputs are incomplete; WEF_OK otherwise.  reset != 0 clears the
+ * word.  The word is shared by all evaluations of the operator.
+ */
+wef_status wef_device_status(wef_op op, int reset);
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* wef_last_error(void);
 

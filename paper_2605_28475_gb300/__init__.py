@@ -47,6 +47,7 @@ def lib():
             "wef_core_build": ([vp, ctypes.c_int, ctypes.c_int, dp, i64], ctypes.c_int),
             "wef_flops": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
             "wef_set_trace_events": ([vp, vp, vp], ctypes.c_int),
+            "wef_device_status": ([vp, ctypes.c_int], ctypes.c_int),
             "wef_last_error": ([], ctypes.c_char_p),
             "wef_destroy": ([vp], ctypes.c_int),
         }
@@ -118,6 +119,10 @@ def wef_flops(op, prec=WEF_FP64):
 
 def wef_set_trace_events(op, ev_start, ev_stop):
     _check(lib().wef_set_trace_events(op, ev_start, ev_stop))
+
+
+def wef_device_status(op, reset=False):
+    _check(lib().wef_device_status(op, 1 if reset else 0))
 
 
 def wef_last_error():

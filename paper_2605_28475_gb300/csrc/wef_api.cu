@@ -62,28 +62,41 @@ struct wef_operator {
   double gamma = 0.0;
   int device = 0;
   int sms = 1;
-  // programs
-  int32_t *d_prog1 = nullptr, *d_off1 = nullptr, *d_w1 = nullptr;
-  double* d_progw1 = nullptr;
-  // chunk bounds for the FP64 path, one set per power-of-two chunk count
-  std::vector<int> chunk_n;    // chunk counts available
-  std::vector<int> chunk_pos;  // offset of each set in d_chunks1
-  int32_t* d_chunks1 = nullptr;
+  // programs: [0] one q1 per task (FP64 path), [1] four q1 per task (tensor-core path)
+  struct DevProg {
+    int32_t *prog = nullptr, *off = nullptr, *w = nullptr, *chunks = nullptr;
+    double* progw = nullptr;
+    std::vector<int> chunk_n, chunk_pos;  // chunk counts available and their offsets in `chunks`
+  } dp[2];
+  int* d_status = nullptr;  // set by kernels whose bounded waits gave up
   // core
-  double* d_R64 = nullptr;  // symmetrised core [sc][k3][k1][k2]
+  double* d_R64 = nullptr;      // symmetrised core [sc][k3][k1][k2]
+  uint8_t* d_Bbf16 = nullptr;   // packed MMA B tiles, BF16
+  uint8_t* d_Btf32 = nullptr;   // packed MMA B tiles, TF32
   bool has_core = false;
   // tracing
   cudaEvent_t trace_start = nullptr, trace_stop = nullptr;
 
-  void release() {
-    cudaFree(d_prog1);
-    cudaFree(d_off1);
-    cudaFree(d_w1);
-    cudaFree(d_progw1);
-    cudaFree(d_chunks1);
+  void release_core() {
     cudaFree(d_R64);
-    d_prog1 = d_off1 = d_w1 = d_chunks1 = nullptr;
-    d_progw1 = d_R64 = nullptr;
+    cudaFree(d_Bbf16);
+    cudaFree(d_Btf32);
+    d_R64 = nullptr;
+    d_Bbf16 = d_Btf32 = nullptr;
+    has_core = false;
+  }
+  void release() {
+    for (auto& d : dp) {
+      cudaFree(d.prog);
+      cudaFree(d.off);
+      cudaFree(d.w);
+      cudaFree(d.chunks);
+      cudaFree(d.progw);
+      d = DevProg();
+    }
+    cudaFree(d_status);
+    d_status = nullptr;
+    release_core();
   }
 };
 
@@ -93,26 +106,31 @@ namespace {
 // first call that needs the GPU so that host-only use (tables, core building)
 // works on machines without one.
 cudaError_t ensure_device(wef_operator* op) {
-  if (op->d_prog1) return cudaSuccess;
+  if (op->d_status) return cudaSuccess;
   cudaError_t e = cudaGetDevice(&op->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&op->sms, cudaDevAttrMultiProcessorCount, op->device);
-  const Program& P = op->T.prog1;
-  if (e == cudaSuccess) e = upload(&op->d_prog1, P.prog);
-  if (e == cudaSuccess) e = upload(&op->d_progw1, P.progw);
-  if (e == cudaSuccess) e = upload(&op->d_off1, P.task_off);
-  if (e == cudaSuccess) e = upload(&op->d_w1, P.task_w);
-  if (e == cudaSuccess) {
-    std::vector<int32_t> all;
-    op->chunk_n.clear();
-    op->chunk_pos.clear();
-    for (int n = 1; n <= P.ntasks(); n *= 2) {
-      std::vector<int32_t> b = split_tasks(P.task_cost, n);
-      op->chunk_n.push_back((int)b.size() - 1);
-      op->chunk_pos.push_back((int)all.size());
-      all.insert(all.end(), b.begin(), b.end());
+  for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    const Program& P = v == 0 ? op->T.prog1 : op->T.prog4;
+    wef_operator::DevProg& D = op->dp[v];
+    e = upload(&D.prog, P.prog);
+    if (e == cudaSuccess) e = upload(&D.progw, P.progw);
+    if (e == cudaSuccess) e = upload(&D.off, P.task_off);
+    if (e == cudaSuccess) e = upload(&D.w, P.task_w);
+    if (e == cudaSuccess) {
+      std::vector<int32_t> all;
+      D.chunk_n.clear();
+      D.chunk_pos.clear();
+      for (int n = 1; n <= P.ntasks(); n *= 2) {
+        std::vector<int32_t> b = split_tasks(P.task_cost, n);
+        D.chunk_n.push_back((int)b.size() - 1);
+        D.chunk_pos.push_back((int)all.size());
+        all.insert(all.end(), b.begin(), b.end());
+      }
+      e = upload(&D.chunks, all);
     }
-    e = upload(&op->d_chunks1, all);
   }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&op->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(op->d_status, 0, sizeof(int));
   if (e != cudaSuccess) op->release();
   return e;
 }
@@ -198,11 +216,30 @@ wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigne
           R64[(((size_t)s * K + k3) * K + k1) * K + k2] = v;
         }
   }
-  cudaFree(op->d_R64);
-  op->d_R64 = nullptr;
-  op->has_core = false;
+  // packed tensor-core B tiles of Rt[sc][k1][k2][k3] (from the FP64 layout [sc][k3][k1][k2])
+  std::vector<uint8_t> Bb, Bt;
+  if (K <= 17) {
+    const int nb = tc_b_tile_bytes(K, false), nt = tc_b_tile_bytes(K, true);
+    Bb.resize((size_t)NS * nb);
+    Bt.resize((size_t)NS * nt);
+    std::vector<double> Rt((size_t)K3);
+    for (int s = 0; s < NS; ++s) {
+      for (int k1 = 0; k1 < K; ++k1)
+        for (int k2 = 0; k2 < K; ++k2)
+          for (int k3 = 0; k3 < K; ++k3)
+            Rt[((size_t)k1 * K + k2) * K + k3] = R64[(((size_t)s * K + k3) * K + k1) * K + k2];
+      tc_pack_b_tile(K, false, Rt.data(), &Bb[(size_t)s * nb]);
+      tc_pack_b_tile(K, true, Rt.data(), &Bt[(size_t)s * nt]);
+    }
+  }
+  op->release_core();
   cudaError_t e = upload(&op->d_R64, R64);
-  if (e != cudaSuccess) return cuda_fail(e, "wef_upload_core");
+  if (e == cudaSuccess) e = upload(&op->d_Bbf16, Bb);
+  if (e == cudaSuccess) e = upload(&op->d_Btf32, Bt);
+  if (e != cudaSuccess) {
+    op->release_core();
+    return cuda_fail(e, "wef_upload_core");
+  }
   op->has_core = true;
   return WEF_OK;
 }
@@ -232,17 +269,25 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
   double* ftile = (double*)workspace;
   cudaError_t e = launch_tile_f(f_dev, ftile, ncells, K, NQ, s);
   if (e != cudaSuccess) return cuda_fail(e, "wef_evaluate: tile kernel");
-  if (prec != WEF_FP64) return fail(WEF_EINVAL, "wef_evaluate: precision not available");
+  if (prec != WEF_FP64 && prec != WEF_MIXED_BF16 && prec != WEF_MIXED_TF32)
+    return fail(WEF_EINVAL, "wef_evaluate: unknown precision");
   // chunk count: enough CTAs for several waves of the GPU
+  const int v = prec == WEF_FP64 ? 0 : 1;
+  const wef_operator::DevProg& D = op->dp[v];
   const int64_t ntiles = (ncells + 31) / 32;
   const int64_t want = 4LL * op->sms;
   int idx = 0;
-  while (idx + 1 < (int)op->chunk_n.size() && ntiles * op->chunk_n[idx] < want) ++idx;
-  DevProgram p{op->d_prog1, op->d_progw1, op->d_off1, op->d_w1, op->T.prog1.ntasks()};
+  while (idx + 1 < (int)D.chunk_n.size() && ntiles * D.chunk_n[idx] < want) ++idx;
+  const Program& P = v == 0 ? op->T.prog1 : op->T.prog4;
+  DevProgram p{D.prog, D.progw, D.off, D.w, P.ntasks()};
   if (op->trace_start) cudaEventRecord(op->trace_start, s);
-  e = launch_fp64(K, ftile, q_dev, ncells, NQ, p, op->d_chunks1 + op->chunk_pos[idx], op->chunk_n[idx], op->d_R64, s);
+  if (prec == WEF_FP64)
+    e = launch_fp64(K, ftile, q_dev, ncells, NQ, p, D.chunks + D.chunk_pos[idx], D.chunk_n[idx], op->d_R64, s);
+  else
+    e = launch_tc(K, prec == WEF_MIXED_TF32, ftile, q_dev, ncells, NQ, p, D.chunks + D.chunk_pos[idx], D.chunk_n[idx],
+                  prec == WEF_MIXED_TF32 ? op->d_Btf32 : op->d_Bbf16, op->d_status, s);
   if (op->trace_stop) cudaEventRecord(op->trace_stop, s);
-  if (e != cudaSuccess) return cuda_fail(e, "wef_evaluate: fp64 kernel");
+  if (e != cudaSuccess) return cuda_fail(e, "wef_evaluate: contraction kernel");
   return WEF_OK;
 }
 
@@ -282,6 +327,17 @@ wef_status wef_set_trace_events(wef_op op, void* ev_start, void* ev_stop) {
   if (!op) return fail(WEF_EINVAL, "wef_set_trace_events: op is NULL");
   op->trace_start = (cudaEvent_t)ev_start;
   op->trace_stop = (cudaEvent_t)ev_stop;
+  return WEF_OK;
+}
+
+wef_status wef_device_status(wef_op op, int reset) {
+  if (!op) return fail(WEF_EINVAL, "wef_device_status: op is NULL");
+  if (!op->d_status) return WEF_OK;
+  int h = 0;
+  cudaError_t e = cudaMemcpy(&h, op->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "wef_device_status");
+  if (reset) cudaMemset(op->d_status, 0, sizeof(int));
+  if (h != 0) return fail(WEF_ETIMEOUT, "a bounded device-side wait gave up in an earlier evaluation");
   return WEF_OK;
 }
 

@@ -126,3 +126,54 @@ def test_error_paths():
     assert e.value.status == W.WEF_EINVAL
     with pytest.raises(W.WefError):
         W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), 4, 0, ws.data_ptr(), 16, 0)
+
+
+# ------------------------------------------------------------------ mixed precision (tcgen05)
+# Normwise bound max|Q - Q_oracle| / max|Q_oracle| for the radial stage in BF16 / TF32 with
+# FP32 accumulation (Phi and the core rounded to 8 / 10 mantissa bits).
+MIXED_TOL = {"bf16": 3e-2, "tf32": 5e-3}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("km,lm,ncells", [(1, 2, 1), (2, 3, 70), (4, 4, 33), (4, 6, 40), (8, 8, 37), (16, 2, 45), (12, 12, 3)])
+def test_mixed_random_core(prec, km, lm, ncells):
+    nt = len(gaunt.channels(lm))
+    R = wi.random_core(nt, km, seed=km * 100 + lm + 1)
+    f = wi.random_cells(km, lm, ncells, seed=lm + 1)
+    op = W.Operator(km, lm, 0.0)
+    op.upload_core(R)
+    Q = _gpu_eval(op, f, prec)
+    W.wef_device_status(op.h)
+    err = _rel(Q, _oracle(km, lm, R, f))
+    print(f"{prec} K={km} L={lm} n={ncells} normwise err {err:.3e}")
+    assert err <= MIXED_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_mixed_invariants_exact(prec):
+    km, lm = 4, 4
+    R = wi.random_core(len(gaunt.channels(lm)), km, seed=3)
+    op = W.Operator(km, lm, 0.0)
+    op.upload_core(R)
+    f = wi.random_cells(km, lm, 50, seed=4)
+    f[0] = 0.0
+    f[0, 0, 0] = 1.0
+    Q = _gpu_eval(op, f, prec)
+    assert np.all(Q[:, 0, 0:4] == 0.0) and np.all(Q[:, 1, 0] == 0.0)
+    assert np.all(Q[0] == 0.0)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_mixed_full_size_sampled(prec):
+    km = lm = 12
+    ncells = 16384
+    R = wi.random_core(len(gaunt.channels(lm)), km, seed=7)
+    f = wi.two_maxwellians(km, lm, ncells, seed=3, pool=512)
+    op = W.Operator(km, lm, 1.0)
+    op.upload_core(R)
+    Q = _gpu_eval(op, f, prec)
+    W.wef_device_status(op.h)
+    idx = np.array([0, 4097, 9999, ncells - 1])
+    err = _rel(Q[idx], _oracle(km, lm, R, f[idx]))
+    print(f"{prec} full-size normwise err {err:.3e}")
+    assert err <= MIXED_TOL[prec]
