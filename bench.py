@@ -6,8 +6,11 @@ mixture projected onto the basis; core from the library's own quadrature.
 The batch (288 MB of f in, 288 MB of Q out) is larger than the 129 MB L2, so no
 flush is needed between steps.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16|tf32] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32|bf16|fp64] [--impl ours|reference]
 
+The headline is the mixed path (FP64 angular coupling, radial stage on the tensor
+cores; TF32 by default); the same run also times the other two precisions with the
+same protocol and reports them under "variants" with the speedup over plain FP64.
 Prints one JSON line (rank 0).  Under torchrun every rank evaluates its own batch
 (weak scaling, no data-path collective); the barrier and the max over ranks of
 the timed region are the only collectives.
@@ -40,7 +43,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "bf16", "tf32"])
+    ap.add_argument("--precision", default="tf32", choices=["fp64", "bf16", "tf32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ncells", type=int, default=NCELLS)
     ap.add_argument("--cpu-sample-rows", type=int, default=384)
@@ -163,7 +166,6 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
-    prec = W.PRECISIONS[args.precision]
     op = W.Operator(KMAX, LMAX, GAMMA)
     R = op.build_core()
     op.upload_core(R)
@@ -172,41 +174,67 @@ def main():
     f = torch.from_numpy(f_host).to(dev)
     q = torch.empty_like(f)
     stream = torch.cuda.current_stream(dev)
-    ws = op.workspace(ncells, prec, dev)
 
-    def step(ev=None):
-        if ev is not None:
-            W.wef_set_trace_events(op.h, ev[0].cuda_event, ev[1].cuda_event)
-        W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), ncells, prec, ws.data_ptr(), ws.numel(), stream.cuda_stream)
+    def measure(precision, with_clocks=False):
+        prec = W.PRECISIONS[precision]
+        ws = op.workspace(ncells, prec, dev)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize(dev)
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for a, b in kev:  # torch creates the CUDA events lazily, on first record
-        a.record(stream)
-        b.record(stream)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    with ClockSampler(local) as clk:
+        def step(ev=None):
+            if ev is not None:
+                W.wef_set_trace_events(op.h, ev[0].cuda_event, ev[1].cuda_event)
+            W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), ncells, prec, ws.data_ptr(), ws.numel(), stream.cuda_stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in kev:  # torch creates the CUDA events lazily, on first record
+            a.record(stream)
+            b.record(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        clk = ClockSampler(local) if with_clocks else None
+        if clk:
+            clk.__enter__()
         e0.record(stream)
         for i in range(args.steps):
             step(kev[i])
         e1.record(stream)
         torch.cuda.synchronize(dev)
-    W.wef_set_trace_events(op.h, None, None)
-    ms_total = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-        dist.barrier()
-    ms_step = ms_total / args.steps
-    value = world * ncells / (ms_step / 1e3)
-    kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
-    fp64_flops, tc_flops = W.wef_flops(op.h, prec)
+        if clk:
+            clk.__exit__()
+        W.wef_set_trace_events(op.h, None, None)
+        W.wef_device_status(op.h)
+        ms_total = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms_total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_total = float(t.item())
+            dist.barrier()
+        ms_step = ms_total / args.steps
+        kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+        fp64_flops, tc_flops = W.wef_flops(op.h, prec)
+        out = {
+            "value": world * ncells / (ms_step / 1e3),
+            "ms_per_step": ms_step,
+            "kernel_ms": kernel_ms,
+            "fp64_tflops": fp64_flops * ncells / (kernel_ms / 1e3) / 1e12,
+            "fp64_flops_per_cell": fp64_flops,
+            "tc_flops_per_cell": tc_flops,
+            "tc_tflops": tc_flops * ncells / (kernel_ms / 1e3) / 1e12,
+            "step": step,
+            "clocks": clk.summary() if clk else None,
+        }
+        return out
+
+    variants = {}
+    order = [p for p in ("fp64", "bf16", "tf32") if p != args.precision] + [args.precision]
+    for pr in order:
+        variants[pr] = measure(pr, with_clocks=(pr == args.precision))
+    head = variants[args.precision]
+    step = head["step"]
     # end to end through the public API: pinned host f -> device, evaluate, Q -> pinned host
     f_pin = torch.from_numpy(f_host).pin_memory()
     q_pin = torch.empty_like(f_pin).pin_memory()
@@ -228,15 +256,15 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    achieved = fp64_flops * ncells / (kernel_ms / 1e3) / 1e12
+    achieved = head["fp64_tflops"]
     line = {
         "metric": METRIC,
-        "value": value,
+        "value": head["value"],
         "unit": "cells/s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms_step,
+        "ms_per_step": head["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -250,15 +278,20 @@ def main():
         },
         "roofline": {
             "bound": "alu",
-            "kernel": "fp64_kernel (angular coupling + FP64 radial)" if args.precision == "fp64" else "mixed kernel",
+            "pipe": "FP64 FMA (angular coupling" + (" + radial contraction)" if args.precision == "fp64" else ")"),
+            "kernel": "fp64_kernel" if args.precision == "fp64" else f"tc_kernel<{KMAX + 1},{args.precision}>",
             "achieved": achieved,
             "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": None,
-            "fp64_flops_per_cell": fp64_flops,
-            "kernel_ms": kernel_ms,
+            "fp64_flops_per_cell": head["fp64_flops_per_cell"],
+            "tc_flops_per_cell": head["tc_flops_per_cell"],
+            "tc_tflops": head["tc_tflops"],
+            "kernel_ms": head["kernel_ms"],
         },
+        "variants": {k: {kk: vv for kk, vv in v.items() if kk not in ("step", "clocks")} for k, v in variants.items()},
+        "speedup_vs_fp64": head["value"] / variants["fp64"]["value"],
         "e2e": {
             "value": world * ncells / (e2e_ms / 1e3),
             "unit": "cells/s",
@@ -266,7 +299,7 @@ def main():
             "d2h_bytes_per_step": int(q_pin.numel() * 8),
         },
         "gpu_launches": 2 * args.steps,
-        "clocks": clk.summary(),
+        "clocks": head["clocks"],
     }
     if world == 1 and os.environ.get("WEF_BENCH_NO_CPU") != "1":
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_cells, args.cpu_sample_rows)

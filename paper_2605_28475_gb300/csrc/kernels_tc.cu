@@ -41,8 +41,11 @@ __device__ __forceinline__ uint32_t a_offset(int row, int k, int esz, int sbo) {
   return (uint32_t)((row >> 3) * sbo + ((k * esz) >> 4) * 128 + (row & 7) * 16 + ((k * esz) & 15));
 }
 
+template <int K>
+__host__ __device__ constexpr int tc_warps() { return K < 4 ? 4 : K; }
+
 template <int K, bool TF32>
-__global__ void __launch_bounds__(32 * K, 1) tc_kernel(const double* __restrict__ ftile, double* __restrict__ qout,
+__global__ void __launch_bounds__(32 * tc_warps<K>(), 1) tc_kernel(const double* __restrict__ ftile, double* __restrict__ qout,
                                                        int64_t ncells, int NQ, const int32_t* __restrict__ prog,
                                                        const double* __restrict__ progw,
                                                        const int32_t* __restrict__ task_off,
@@ -64,7 +67,10 @@ __global__ void __launch_bounds__(32 * K, 1) tc_kernel(const double* __restrict_
   const int64_t cell = tile * 32 + lane;
 
   // zero the A tile once: padding columns (k >= K*K) and unused rows stay zero
-  for (int i = tid; i < S::A_BYTES / 16; i += 32 * K) ((uint4*)sA)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < S::A_BYTES / 16; i += 32 * tc_warps<K>()) ((uint4*)sA)[i] = make_uint4(0, 0, 0, 0);
+  // with K < 4 the block still has 4 warps so that every TMEM lane quarter is drained;
+  // the extra warps do no angular work
+  const bool active = k3 < K;
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&tma_bar[b], 1);
@@ -114,6 +120,14 @@ __global__ void __launch_bounds__(32 * K, 1) tc_kernel(const double* __restrict_
       p += 1 + nslots;
       const int buf = g & 1;  // B tile buffer and MMA barrier of this channel
       for (int s = 0; s < nslots; ++s) {
+        if (!active) {
+          for (int gi = 0; gi < ngs[s]; ++gi) {
+            const int ne = __ldg(p) >> 16;
+            p += 1 + ne;
+            pw += ne;
+          }
+          continue;
+        }
         double Phi[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) Phi[k] = 0.0;
@@ -274,7 +288,7 @@ cudaError_t launch_tc_k(const double* ftile, double* q, int64_t ncells, int NQ, 
     attr = true;
   }
   dim3 grid((unsigned)ntiles, (unsigned)nchunks);
-  tc_kernel<K, TF32><<<grid, 32 * K, S::SMEM, s>>>(ftile, q, ncells, NQ, p.prog, p.progw, p.task_off, p.task_w, chunks,
+  tc_kernel<K, TF32><<<grid, 32 * tc_warps<K>(), S::SMEM, s>>>(ftile, q, ncells, NQ, p.prog, p.progw, p.task_off, p.task_w, chunks,
                                                   Btiles, status);
   return cudaGetLastError();
 }
