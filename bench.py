@@ -48,7 +48,29 @@ def parse():
     ap.add_argument("--ncells", type=int, default=NCELLS)
     ap.add_argument("--cpu-sample-rows", type=int, default=384)
     ap.add_argument("--cpu-sample-cells", type=int, default=4)
+    ap.add_argument("--workload", default="kl12", choices=["kl12", "maxwell4", "hs8", "ragged", "serve"],
+                    help="kl12: hard spheres K=L=12 x 16384 cells (default); maxwell4: one Maxwell cell at "
+                         "K=L=4; hs8: hard spheres K=L=8 x 4096 cells; ragged: VHS, 32768 cells with "
+                         "(Kmax, Lmax) drawn from {6,8,10,12,16}; serve: Poisson request stream")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     return ap.parse_args()
+
+
+def max_over_ranks(ms_local, dist, device=None):
+    """The timed region's duration as the max over ranks (every rank gets it)."""
+    if dist is None:
+        return ms_local
+    import torch
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(world, ncells_per_rank, ms_step):
+    """Whole-job cells/s: all ranks' cells divided by the (max over ranks) step time."""
+    return world * ncells_per_rank / (ms_step / 1e3)
 
 
 def dist_env():
@@ -135,6 +157,18 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def fp64_probe():
+    """Live FP64 FMA pipe throughput from the package's probe utility (None if not built)."""
+    exe = os.path.join(ROOT, "paper_2605_28475_gb300", "_build", "fp64_peak")
+    if not os.path.exists(exe):
+        return None
+    try:
+        out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+        return json.loads(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+    except (OSError, ValueError, subprocess.TimeoutExpired, IndexError):
+        return None
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -147,6 +181,138 @@ def run_reference(args, rank, world):
         "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+
+# ------------------------------------------------------------------ further workloads
+def _line(metric, value, unit, ms, args, world, dtype, workload, hib=True, **kw):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+         "ms_per_step": ms, "higher_is_better": hib, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+         "data": "synthetic", "config": {"workload": workload}}
+    d.update(kw)
+    return d
+
+
+def _time_steps(step, steps, warmup, stream, torch):
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def bench_small(args, W, torch, dev, world, kind):
+    """maxwell4: one perturbed-Maxwellian cell, Maxwell molecules, K=L=4, FP64 (latency);
+    hs8: 4096 two-Maxwellian cells, hard spheres, K=L=8, FP64 (cells/s)."""
+    import wef_inputs as wi
+
+    if kind == "maxwell4":
+        km, gamma, n, f_host = 4, 0.0, 1, wi.perturbed_maxwellian(4, 4, 1, seed=1)
+    else:
+        km, gamma, n, f_host = 8, 1.0, 4096, wi.two_maxwellians(8, 8, 4096, seed=2, pool=1024)
+    op = W.Operator(km, km, gamma)
+    op.upload_core(op.build_core())
+    f = torch.from_numpy(f_host).to(dev)
+    q = torch.empty_like(f)
+    st = torch.cuda.current_stream(dev)
+    ws = op.workspace(n, 0, dev)
+    step = lambda: W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), n, 0, ws.data_ptr(), ws.numel(), st.cuda_stream)  # noqa: E731
+    ms = _time_steps(step, max(args.steps, 20), args.warmup, st, torch)
+    fp64_flops, _ = W.wef_flops(op.h, 0)
+    wl = ("Maxwell molecules, Kmax=Lmax=4, 1 perturbed-Maxwellian cell, FP64" if kind == "maxwell4" else
+          "hard spheres, Kmax=Lmax=8, 4096 two-Maxwellian cells, FP64")
+    if kind == "maxwell4":
+        return _line("Q(f,f) latency, 1 cell, K=L=4", ms * 1e3, "us", ms, args, world, "f64", wl, hib=False,
+                     fp64_flops_per_cell=fp64_flops)
+    return _line("Q(f,f) cell-evals/s at K=L=8", n / (ms / 1e3), "cells/s", ms, args, world, "f64", wl,
+                 roofline={"bound": "alu", "achieved": fp64_flops * n / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                           "unit": "TFLOP/s", "frac": fp64_flops * n / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                           "note": "whole step (re-tiling + contraction)"})
+
+
+def bench_ragged(args, W, torch, dev, world, ncells=32768, seed=4):
+    """VHS gamma=0.5, ncells cells with (Kmax, Lmax) drawn independently from {6,8,10,12,16},
+    grouped by shape; one persistent TF32 launch replayed from a CUDA graph, autotuned."""
+    import wef_inputs as wi
+
+    vals = [6, 8, 10, 12, 16]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    draws = rng.integers(0, 5, (ncells, 2))
+    shapes = [(vals[a], vals[b]) for a in range(5) for b in range(5)]
+    counts = [int(np.sum((draws[:, 0] == a) & (draws[:, 1] == b))) for a in range(5) for b in range(5)]
+    ops, fs = [], []
+    real = os.environ.get("WEF_BENCH_QUADRATURE_CORES") == "1"
+    for i, ((km, lm), n) in enumerate(zip(shapes, counts)):
+        op = W.Operator(km, lm, 0.5)
+        R = op.build_core() if real else wi.random_core(op.n_channels, km, seed=100 + i)
+        op.upload_core(R)
+        ops.append(op)
+        fs.append(wi.two_maxwellians(km, lm, n, seed=200 + i, pool=min(256, max(n, 1))).reshape(-1))
+    f = torch.from_numpy(np.concatenate(fs)).to(dev)
+    q = torch.empty_like(f)
+    plan = W.wef_plan_create([o.h for o in ops], counts, W.WEF_MIXED_TF32, 0)
+    ws = torch.empty(W.wef_plan_workspace_size(plan), dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    g = W.wef_plan_autotune(plan, f.data_ptr(), q.data_ptr(), ws.data_ptr(), ws.numel(), st.cuda_stream)
+    step = lambda: W.wef_plan_graph_launch(plan, f.data_ptr(), q.data_ptr(), ws.data_ptr(), ws.numel(), st.cuda_stream)  # noqa: E731
+    ms = _time_steps(step, args.steps, args.warmup, st, torch)
+    W.wef_plan_status(plan)
+    flops = sum(W.wef_flops(o.h, W.WEF_MIXED_TF32)[0] * n for o, n in zip(ops, counts))
+    achieved = flops / (ms / 1e3) / 1e12
+    W.wef_plan_destroy(plan)
+    return _line("Q(f,f) cell-evals/s, ragged (Kmax,Lmax) in {6..16}^2", ncells / (ms / 1e3), "cells/s", ms, args, world,
+                 "f64+tf32",
+                 f"VHS gamma=0.5, {ncells} cells, (Kmax, Lmax) drawn independently per cell, 25 shapes grouped; one "
+                 f"persistent launch under a CUDA graph; autotuned granularity {g}; cores "
+                 + ("from the library quadrature" if real else "random stand-ins (timing does not depend on values)"),
+                 roofline={"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": achieved / FP64_PEAK_TFLOPS, "fp64_flops_total": flops},
+                 gpu_launches=2 * args.steps)
+
+
+def bench_serve(args, W, torch, dev, world):
+    """Poisson stream of requests (1-4096 cells, Kmax=Lmax in {8,10,12,16}, hard spheres),
+    continuous batching with memory admission; rate = 0.7 x measured capacity."""
+    import wef_inputs as wi
+    from paper_2605_28475_gb300 import serve
+
+    shapes = [(8, 8), (10, 10), (12, 12), (16, 16)]
+    real = os.environ.get("WEF_BENCH_QUADRATURE_CORES") == "1"
+    ops = {}
+    for i, (km, lm) in enumerate(shapes):
+        op = W.Operator(km, lm, 1.0)
+        op.upload_core(op.build_core() if real else wi.random_core(op.n_channels, km, seed=300 + i))
+        ops[(km, lm)] = op
+    # capacity: full-batch TF32 throughput per shape, in FP64 flops/s
+    st = torch.cuda.current_stream(dev)
+    cap = {}
+    for sh, op in ops.items():
+        n = 2048
+        f = torch.from_numpy(wi.random_cells(sh[0], sh[1], n, seed=1)).to(dev)
+        q = torch.empty_like(f)
+        ws = op.workspace(n, W.WEF_MIXED_TF32, dev)
+        step = lambda: W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), n, W.WEF_MIXED_TF32, ws.data_ptr(), ws.numel(), st.cuda_stream)  # noqa: E731,B023
+        ms = _time_steps(step, 3, 1, st, torch)
+        cap[sh] = n / (ms / 1e3)  # cells/s at this shape
+    max_cells = 4096
+    # mean service time of a request (log-uniform size, uniform shape) at full-batch speed
+    sizes = np.exp(np.linspace(0, np.log(max_cells), 2001))
+    mean_cells = float(np.mean(sizes))
+    mean_service = float(np.mean([mean_cells / cap[sh] for sh in shapes]))
+    rate = 0.7 / mean_service
+    reqs = serve.poisson_requests(rate, args.duration, shapes, max_cells, seed=5,
+                                  make_cells=lambda sh, n, s: wi.random_cells(sh[0], sh[1], n, seed=s))
+    srv = serve.Server(ops, arena_bytes=24 << 30, nslots=8, precision="tf32", device=str(dev))
+    res = serve.run(srv, reqs)
+    return _line("serve: p50/p99 latency and cells/s", res["cells_per_s"], "cells/s", None, args, world, "f64+tf32",
+                 f"Poisson arrivals at 0.7x capacity ({rate:.1f} req/s) for {args.duration:.0f} s; sizes log-uniform "
+                 f"1-{max_cells} cells; Kmax=Lmax in {{8,10,12,16}}; 8 stream slots; 24 GiB admission arena",
+                 serving=res, capacity_cells_per_s={f"{k[0]}x{k[1]}": v for k, v in cap.items()})
 
 
 def main():
@@ -166,6 +332,18 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
+    if args.workload != "kl12":
+        fn = {"maxwell4": lambda: bench_small(args, W, torch, dev, world, "maxwell4"),
+              "hs8": lambda: bench_small(args, W, torch, dev, world, "hs8"),
+              "ragged": lambda: bench_ragged(args, W, torch, dev, world),
+              "serve": lambda: bench_serve(args, W, torch, dev, world)}[args.workload]
+        line = fn()
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
+    probe = fp64_probe() if rank == 0 else None
     op = W.Operator(KMAX, LMAX, GAMMA)
     R = op.build_core()
     op.upload_core(R)
@@ -207,17 +385,12 @@ def main():
             clk.__exit__()
         W.wef_set_trace_events(op.h, None, None)
         W.wef_device_status(op.h)
-        ms_total = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms_total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_total = float(t.item())
-            dist.barrier()
+        ms_total = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         ms_step = ms_total / args.steps
         kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
         fp64_flops, tc_flops = W.wef_flops(op.h, prec)
         out = {
-            "value": world * ncells / (ms_step / 1e3),
+            "value": job_throughput(world, ncells, ms_step),
             "ms_per_step": ms_step,
             "kernel_ms": kernel_ms,
             "fp64_tflops": fp64_flops * ncells / (kernel_ms / 1e3) / 1e12,
@@ -289,6 +462,8 @@ def main():
             "tc_flops_per_cell": head["tc_flops_per_cell"],
             "tc_tflops": head["tc_tflops"],
             "kernel_ms": head["kernel_ms"],
+            "peak_note": "peak = 152 SMs x 2 DFMA lanes/clock x 2 flop x 2070 MHz; probe = live DFMA chain",
+            "peak_probe": probe,
         },
         "variants": {k: {kk: vv for kk, vv in v.items() if kk not in ("step", "clocks")} for k, v in variants.items()},
         "speedup_vs_fp64": head["value"] / variants["fp64"]["value"],

@@ -111,6 +111,42 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
                         void* workspace, int64_t workspace_bytes, void* stream);
 
 /*
+ * Ragged batches (several (Kmax, Lmax) operators in one launch).
+ *
+ * A plan covers the cells of nops operators stored back to back in one buffer:
+ * first ncells[0] cells of ops[0] (each K0*NQ0 doubles, layout as above), then
+ * ncells[1] cells of ops[1], and so on; Q uses the same layout.  It evaluates them
+ * with one re-tiling launch and one persistent tensor-core launch (one CTA per SM
+ * pulling (shape, tile, task range) work items from a device queue, longest
+ * first).  granularity = how many task ranges each 32-cell tile is split into
+ * (0 = from the tuning cache named by the WEF_TUNE_CACHE environment variable,
+ * else about 8 items per SM).  Precision: WEF_MIXED_TF32 or WEF_MIXED_BF16.
+ * Every operator must have a core uploaded (Kmax >= 1) and must outlive the plan.
+ * Set-up allocations happen in wef_plan_create only.
+ */
+typedef struct wef_plan_s* wef_plan;
+wef_status wef_plan_create(const wef_op* ops, const int64_t* ncells, int nops, wef_precision prec, int granularity,
+                           wef_plan* out);
+/* Bytes of device workspace (256-byte aligned) the plan's launches need. */
+wef_status wef_plan_workspace_size(wef_plan plan, int64_t* bytes);
+/* Asynchronous evaluation on `stream`; allocates nothing. */
+wef_status wef_plan_execute(wef_plan plan, const double* f_dev, double* q_dev, void* workspace, int64_t ws_bytes,
+                            void* stream);
+/* Same, replayed from a CUDA graph: the first call (and any call with different
+ * buffers) captures the launches on the plan's own stream and instantiates the
+ * graph; later calls only launch it on `stream`. */
+wef_status wef_plan_graph_launch(wef_plan plan, const double* f_dev, double* q_dev, void* workspace,
+                                 int64_t ws_bytes, void* stream);
+/* Autotuner: times the plan at granularities 1, 2, 4, ... on the given buffers
+ * (synchronous), keeps the fastest, appends it to the WEF_TUNE_CACHE file if set,
+ * and returns it in *chosen (may be NULL). */
+wef_status wef_plan_autotune(wef_plan plan, const double* f_dev, double* q_dev, void* workspace, int64_t ws_bytes,
+                             void* stream, int* chosen);
+/* Synchronous check of the plan's device status word (see wef_device_status). */
+wef_status wef_plan_status(wef_plan plan, int reset);
+wef_status wef_plan_destroy(wef_plan plan);
+
+/*
  * wef_core_build - the kinematic core R[c][k1][k2][k3] of the operator by the
  * singular quadrature of Sec. 4.3 / Appendix A-B, on the host (all cores of the
  * machine).  pad_rad / pad_ang are the selective paddings of Appendix B (the

@@ -48,6 +48,13 @@ def lib():
             "wef_flops": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
             "wef_set_trace_events": ([vp, vp, vp], ctypes.c_int),
             "wef_device_status": ([vp, ctypes.c_int], ctypes.c_int),
+            "wef_plan_create": ([ctypes.POINTER(vp), i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)], ctypes.c_int),
+            "wef_plan_workspace_size": ([vp, i64p], ctypes.c_int),
+            "wef_plan_execute": ([vp, vp, vp, vp, i64, vp], ctypes.c_int),
+            "wef_plan_graph_launch": ([vp, vp, vp, vp, i64, vp], ctypes.c_int),
+            "wef_plan_autotune": ([vp, vp, vp, vp, i64, vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "wef_plan_status": ([vp, ctypes.c_int], ctypes.c_int),
+            "wef_plan_destroy": ([vp], ctypes.c_int),
             "wef_last_error": ([], ctypes.c_char_p),
             "wef_destroy": ([vp], ctypes.c_int),
         }
@@ -123,6 +130,43 @@ def wef_set_trace_events(op, ev_start, ev_stop):
 
 def wef_device_status(op, reset=False):
     _check(lib().wef_device_status(op, 1 if reset else 0))
+
+
+def wef_plan_create(ops, ncells, prec=WEF_MIXED_TF32, granularity=0):
+    n = len(ops)
+    arr = (ctypes.c_void_p * n)(*[o.value if isinstance(o, ctypes.c_void_p) else o for o in ops])
+    cnt = (ctypes.c_int64 * n)(*[int(c) for c in ncells])
+    h = ctypes.c_void_p()
+    _check(lib().wef_plan_create(arr, cnt, n, int(prec), int(granularity), ctypes.byref(h)))
+    return h
+
+
+def wef_plan_workspace_size(plan):
+    b = ctypes.c_int64()
+    _check(lib().wef_plan_workspace_size(plan, ctypes.byref(b)))
+    return b.value
+
+
+def wef_plan_execute(plan, f_ptr, q_ptr, ws_ptr, ws_bytes, stream_ptr):
+    _check(lib().wef_plan_execute(plan, f_ptr, q_ptr, ws_ptr, int(ws_bytes), stream_ptr))
+
+
+def wef_plan_graph_launch(plan, f_ptr, q_ptr, ws_ptr, ws_bytes, stream_ptr):
+    _check(lib().wef_plan_graph_launch(plan, f_ptr, q_ptr, ws_ptr, int(ws_bytes), stream_ptr))
+
+
+def wef_plan_autotune(plan, f_ptr, q_ptr, ws_ptr, ws_bytes, stream_ptr):
+    g = ctypes.c_int()
+    _check(lib().wef_plan_autotune(plan, f_ptr, q_ptr, ws_ptr, int(ws_bytes), stream_ptr, ctypes.byref(g)))
+    return g.value
+
+
+def wef_plan_status(plan, reset=False):
+    _check(lib().wef_plan_status(plan, 1 if reset else 0))
+
+
+def wef_plan_destroy(plan):
+    _check(lib().wef_plan_destroy(plan))
 
 
 def wef_last_error():

@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwef.so")
+PROBE = os.path.join(OUT_DIR, "fp64_peak")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 
@@ -55,9 +56,13 @@ def build(verbose=False, extra_nvcc=()):
         for lg in logs:
             if lg.strip():
                 print(lg)
-    tmp = LIB + ".tmp"
-    _compile([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"])
-    os.replace(tmp, LIB)
+    jobs_probe = [_nvcc(), *ARCH, "-O3", "-o", PROBE, os.path.join(CSRC, "probes", "fp64_peak.cu")]
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        fut = ex.submit(_compile, jobs_probe)
+        tmp = LIB + ".tmp"
+        _compile([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"])
+        os.replace(tmp, LIB)
+        fut.result()
     return LIB
 
 

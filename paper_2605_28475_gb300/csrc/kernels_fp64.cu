@@ -9,6 +9,7 @@
 // warp-uniform instruction stream (the Program built on the host).
 #include <cuda_runtime.h>
 
+#include "phi.cuh"
 #include "wef_internal.hpp"
 
 namespace wef {
@@ -40,9 +41,8 @@ __global__ void tile_f_kernel(const double* __restrict__ f, double* __restrict__
 template <int K>
 __global__ void __launch_bounds__(32 * K) fp64_kernel(const double* __restrict__ ftile, double* __restrict__ qout,
                                                       int64_t ncells, int NQ, const int32_t* __restrict__ prog,
-                                                      const double* __restrict__ progw,
+                                                      const int4* __restrict__ groups, const double2* __restrict__ gw,
                                                       const int32_t* __restrict__ task_off,
-                                                      const int32_t* __restrict__ task_w,
                                                       const int32_t* __restrict__ chunks,
                                                       const double* __restrict__ R64) {
   extern __shared__ double red[];  // [k3][k1][32]
@@ -53,7 +53,6 @@ __global__ void __launch_bounds__(32 * K) fp64_kernel(const double* __restrict__
   const int64_t cell = tile * 32 + lane;
   for (int t = t0; t < t1; ++t) {
     const int32_t* p = prog + task_off[t];
-    const double* pw = progw + task_w[t];
     const int q1 = __ldg(p);
     const int nchan = __ldg(p + 2);
     p += 3;
@@ -61,30 +60,10 @@ __global__ void __launch_bounds__(32 * K) fp64_kernel(const double* __restrict__
 #pragma unroll
     for (int k = 0; k < K; ++k) P[k] = 0.0;
     for (int ci = 0; ci < nchan; ++ci) {
-      const int sc = __ldg(p);
-      const int ng = __ldg(p + 1);
-      p += 2;
+      const int sc = __ldg(p), g0 = __ldg(p + 1), ng = __ldg(p + 2);
+      p += 3;
       double Phi[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) Phi[k] = 0.0;
-      for (int g = 0; g < ng; ++g) {
-        const int hdr = __ldg(p);
-        const int q2 = hdr & 0xffff, ne = hdr >> 16;
-        ++p;
-        double h = 0.0;
-        for (int e = 0; e < ne; ++e) {
-          const int q3 = __ldg(p + e);
-          h = fma(__ldg(pw + e), __ldg(ft + (q3 * K + k3) * 32), h);
-        }
-        p += ne;
-        pw += ne;
-        const double* f2 = ft + q2 * K * 32;
-        double fv[K];
-#pragma unroll
-        for (int k2 = 0; k2 < K; ++k2) fv[k2] = __ldg(f2 + k2 * 32);
-#pragma unroll
-        for (int k2 = 0; k2 < K; ++k2) Phi[k2] = fma(fv[k2], h, Phi[k2]);
-      }
+      phi_slice<K>(Phi, groups, gw, g0, ng, ft, k3);
       // radial contraction with the symmetrised core, layout R64[sc][k3][k1][k2]
       const double* Rs = R64 + ((int64_t)sc * K + k3) * K * K;
 #pragma unroll
@@ -124,7 +103,7 @@ cudaError_t launch_fp64_k(const double* ftile, double* q, int64_t ncells, int NQ
     attr_set = true;
   }
   dim3 grid((unsigned)ntiles, (unsigned)nchunks);
-  fp64_kernel<K><<<grid, 32 * K, smem, s>>>(ftile, q, ncells, NQ, p.prog, p.progw, p.task_off, p.task_w, chunks, R64);
+  fp64_kernel<K><<<grid, 32 * K, smem, s>>>(ftile, q, ncells, NQ, p.prog, p.groups, p.gw, p.task_off, chunks, R64);
   return cudaGetLastError();
 }
 

@@ -5,20 +5,26 @@
 // over all channels of the output shell -> FP64 epilogue with the Sec. 4.4
 // conservation projection.
 //
-// CTA = 32 cells x K warps (warp = k3, lane = cell).  A task covers up to four
-// q1 of one shell l1; the MMA row is (slot, cell) = 32 * slot + lane, its column
-// k1, and the reduction index (k2, k3) = k2 * K + k3.
+// A CTA works on tiles of 32 cells; warp w is the radial index k3 = w and the
+// lane is the cell.  A task covers up to four q1 of one shell l1; the MMA row is
+// (slot, cell) = 32 * slot + lane, its column k1, and the reduction index
+// (k2, k3) = k2 * K + k3.  `run_tile` does all tasks [t0, t1) of one tile; the
+// one-shape kernel calls it once, the ragged persistent kernel calls it for every
+// work item it pulls from a device queue.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
 
+#include "phi.cuh"
 #include "tc_ptx.cuh"
 #include "wef_internal.hpp"
 
 namespace wef {
 
 namespace {
+
+constexpr int kBarBytes = 1024;  // barriers and the TMEM address sit below the operand tiles
 
 template <int K, bool TF32>
 struct TcShape {
@@ -27,252 +33,308 @@ struct TcShape {
   static constexpr int KSTEP = TF32 ? 8 : 16;                    // reduction elements per MMA
   static constexpr int KP = (KK + KSTEP - 1) / KSTEP * KSTEP;    // padded reduction length
   static constexpr int NN = K <= 16 ? 16 : 32;                   // MMA N (k1, padded)
-  static constexpr int SBO_A = KP * ESZ * 8;                     // bytes between 8-row groups
+  static constexpr int SBO = KP * ESZ * 8;                       // bytes between 8-row groups
   static constexpr int A_BYTES = 128 * KP * ESZ;
   static constexpr int B_BYTES = NN * KP * ESZ;
   static constexpr int NSTEP = KP / KSTEP;
   static constexpr int TMEM_COLS = 2 * NN <= 32 ? 32 : 2 * NN;   // two accumulators
-  static constexpr int OFF_B = A_BYTES;
-  static constexpr int OFF_BAR = OFF_B + 2 * B_BYTES;
-  static constexpr int SMEM = OFF_BAR + 64;
+  static constexpr int OFF_A = kBarBytes;
+  static constexpr int OFF_B = OFF_A + A_BYTES;
+  static constexpr int SMEM = OFF_B + 2 * B_BYTES;
 };
+
+template <int K>
+__host__ __device__ constexpr int tc_warps() {
+  return K < 4 ? 4 : K;
+}
+
+// FP64 -> TF32 / BF16 bit patterns with 32-bit integer instructions on the two
+// halves of the double (the FP64 pipe, GB300's scarcest unit, would otherwise also
+// execute the conversions).  Round to nearest even at the target mantissa width
+// directly from the double; results below the FP32 normal range flush to a signed
+// zero; overflow gives Inf; Inf/NaN are kept.
+template <int MBITS>
+__device__ __forceinline__ uint32_t d2f_bits(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const uint32_t mh = hi & 0xFFFFFu;  // top 20 of the 52 mantissa bits
+  if (e == 0x7FF) return sign | 0x7F800000u | ((mh | lo) ? 0x00400000u : 0u);
+  constexpr int drop = 20 - MBITS;     // bits of mh below the kept mantissa (lo is entirely below)
+  uint32_t m = mh >> drop;
+  const uint32_t rem = mh & ((1u << drop) - 1u), half = 1u << (drop - 1);
+  const bool up = rem > half || (rem == half && (lo != 0u || (m & 1u)));
+  int e32 = e - 1023 + 127;
+  m += up ? 1u : 0u;
+  if (m >> MBITS) {  // mantissa overflow into the exponent
+    m = 0u;
+    ++e32;
+  }
+  if (e == 0 || e32 <= 0) return sign;
+  if (e32 >= 255) return sign | 0x7F800000u;
+  return sign | ((uint32_t)e32 << 23) | (m << (23 - MBITS));
+}
 
 __device__ __forceinline__ uint32_t a_offset(int row, int k, int esz, int sbo) {
   return (uint32_t)((row >> 3) * sbo + ((k * esz) >> 4) * 128 + (row & 7) * 16 + ((k * esz) & 15));
 }
 
-template <int K>
-__host__ __device__ constexpr int tc_warps() { return K < 4 ? 4 : K; }
+// CTA-uniform bookkeeping, one copy per thread.
+struct TcState {
+  uint8_t* smem;
+  uint64_t* tma_bar;  // [2]: B tile landed
+  uint64_t* mma_bar;  // [2]: MMAs of a channel done
+  uint32_t tmem;
+  int g;              // channels issued so far by this CTA (selects buffers and barrier phases)
+  int tma_issued;     // thread 0: channels whose B tile has been requested
+  int tma_waited;     // thread 0: channels whose B tile has landed
+  int failed;
+};
 
-template <int K, bool TF32>
-__global__ void __launch_bounds__(32 * tc_warps<K>(), 1) tc_kernel(const double* __restrict__ ftile, double* __restrict__ qout,
-                                                       int64_t ncells, int NQ, const int32_t* __restrict__ prog,
-                                                       const double* __restrict__ progw,
-                                                       const int32_t* __restrict__ task_off,
-                                                       const int32_t* __restrict__ task_w,
-                                                       const int32_t* __restrict__ chunks,
-                                                       const uint8_t* __restrict__ Btiles, int* __restrict__ status) {
-  using S = TcShape<K, TF32>;
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + S::OFF_B;
-  uint64_t* tma_bar = (uint64_t*)(smem + S::OFF_BAR);  // [2]
-  uint64_t* mma_bar = tma_bar + 2;                      // [2]
-  uint32_t* tmem_s = (uint32_t*)(mma_bar + 2);
-  const int tid = threadIdx.x;
-  const int k3 = tid >> 5, lane = tid & 31;
-  const int64_t tile = blockIdx.x;
-  const int t0 = chunks[blockIdx.y], t1 = chunks[blockIdx.y + 1];
-  const double* ft = ftile + tile * (int64_t)NQ * K * 32 + lane;
-  const int64_t cell = tile * 32 + lane;
-
-  // zero the A tile once: padding columns (k >= K*K) and unused rows stay zero
-  for (int i = tid; i < S::A_BYTES / 16; i += 32 * tc_warps<K>()) ((uint4*)sA)[i] = make_uint4(0, 0, 0, 0);
-  // with K < 4 the block still has 4 warps so that every TMEM lane quarter is drained;
-  // the extra warps do no angular work
-  const bool active = k3 < K;
-  if (tid == 0) {
+__device__ void tc_setup(TcState& st, uint8_t* smem, int tmem_cols) {
+  st.smem = smem;
+  st.tma_bar = (uint64_t*)smem;
+  st.mma_bar = st.tma_bar + 2;
+  uint32_t* tmem_s = (uint32_t*)(st.mma_bar + 2);
+  st.g = st.tma_issued = st.tma_waited = st.failed = 0;
+  if (threadIdx.x == 0) {
     for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&tma_bar[b], 1);
-      tc::mbar_init(&mma_bar[b], 1);
+      tc::mbar_init(&st.tma_bar[b], 1);
+      tc::mbar_init(&st.mma_bar[b], 1);
     }
     tc::fence_mbar_init();
   }
-  if (k3 == 0) tc::tmem_alloc(tmem_s, S::TMEM_COLS);
-  tc::fence_proxy_async();
+  if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(tmem_s, tmem_cols);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tmem = *tmem_s;
-  constexpr uint32_t idesc = tc::instr_desc(TF32 ? 2 : 1, 128, S::NN);
-  const uint32_t sA_u = tc::smem_u32(sA), sB_u = tc::smem_u32(sB);
-  int failed = 0;
-  int tma_issued = 0, tma_waited = 0;  // thread 0 only
+  st.tmem = *tmem_s;
+}
 
-  // global channel counter g over the CTA's tasks: A/B buffers and barrier phases
-  int g = 0;
-  int pend_task_slots = 0, pend_q1 = 0, pend_acc = 0, pend_g = -1;  // epilogue pending for the previous task
-  // first B tile
-  if (tid == 0 && t0 < t1) {
-    const int32_t* p = prog + task_off[t0];
-    if (p[2] > 0) {
-      tc::mbar_expect_tx(&tma_bar[0], S::B_BYTES);
-      tc::bulk_g2s(sB, Btiles + (size_t)p[3] * S::B_BYTES, S::B_BYTES, &tma_bar[0]);
-      tma_issued = 1;
+// Wait (bounded) for outstanding MMAs and bulk copies, then free TMEM.
+__device__ void tc_teardown(TcState& st, int tmem_cols, int* status) {
+  if (st.failed && threadIdx.x == 0) atomicExch(status, 1);
+  if (threadIdx.x == 0) {
+    if (st.g >= 1) tc::mbar_wait(&st.mma_bar[(st.g - 1) & 1], ((st.g - 1) >> 1) & 1);
+    if (st.tma_issued > st.tma_waited) {
+      const int gp = st.tma_issued - 1;
+      tc::mbar_wait(&st.tma_bar[gp & 1], (gp >> 1) & 1);
     }
   }
-  for (int t = t0; t < t1 && !failed; ++t) {
+  tc::tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(st.tmem, tmem_cols);
+}
+
+// Epilogue of one task: TMEM accumulator -> FP64 -> projection -> Q (warps 0-3).
+template <int K, bool TF32>
+__device__ __forceinline__ void tc_epilogue(TcState& st, int last_g, int acc, int q1b, int nslots, double* qout,
+                                            int64_t cell, int64_t ncells, int NQ) {
+  using S = TcShape<K, TF32>;
+  const int w = threadIdx.x >> 5;
+  if (w >= 4) return;
+  if (!tc::mbar_wait(&st.mma_bar[last_g & 1], (last_g >> 1) & 1)) st.failed = 1;
+  tc::tc_fence_after();
+  float v[16];
+  const uint32_t ta = st.tmem + ((uint32_t)(32 * w) << 16) + acc * S::NN;
+  tc::tmem_ld16(ta, v);
+  const int q1 = q1b + w;
+  const bool store = w < nslots && cell < ncells;
+  double* qc = qout + cell * (int64_t)K * NQ + q1;
+  if (store) {
+#pragma unroll
+    for (int k1 = 0; k1 < (K < 16 ? K : 16); ++k1) {
+      double val = (double)v[k1];
+      if ((k1 == 0 && q1 < 4) || (k1 == 1 && q1 == 0)) val = 0.0;  // conservation projection
+      qc[(int64_t)k1 * NQ] = val;
+    }
+  }
+  if constexpr (S::NN > 16) {
+    tc::tmem_ld16(ta + 16, v);
+    if (store) {
+#pragma unroll
+      for (int k1 = 16; k1 < K; ++k1) qc[(int64_t)k1 * NQ] = (double)v[k1 - 16];
+    }
+  }
+  tc::tc_fence_before();
+}
+
+// All tasks [t0, t1) of one 32-cell tile.  ft = tile base of the re-tiled f;
+// cell = this lane's cell index within its batch; qout = that batch's Q.
+template <int K, bool TF32>
+__device__ void run_tile(TcState& st, const double* __restrict__ ft, double* __restrict__ qout, int64_t cell,
+                         int64_t ncells, int NQ, const int32_t* __restrict__ prog, const int4* __restrict__ groups,
+                         const double2* __restrict__ gw, const int32_t* __restrict__ task_off, int t0, int t1,
+                         const uint8_t* __restrict__ Btiles, int* __restrict__ status) {
+  using S = TcShape<K, TF32>;
+  const int tid = threadIdx.x;
+  const int k3 = tid >> 5, lane = tid & 31;
+  const bool active = k3 < K;  // extra warps (K < 4, or a wider persistent block) do no angular work
+  uint8_t* sA = st.smem + S::OFF_A;
+  uint8_t* sB = st.smem + S::OFF_B;
+  const uint32_t sA_u = tc::smem_u32(sA), sB_u = tc::smem_u32(sB);
+  constexpr uint32_t idesc = tc::instr_desc(TF32 ? 2 : 1, 128, S::NN);
+  ft += lane;
+  // zero the A tile: padding columns (k >= K*K) and unused rows stay zero.  The last
+  // MMA that read A (channel g-1) has completed: every earlier call ended with an epilogue.
+  for (int i = tid; i < S::A_BYTES / 16; i += blockDim.x) ((uint4*)sA)[i] = make_uint4(0, 0, 0, 0);
+  tc::fence_proxy_async();
+  __syncthreads();
+  if (tid == 0 && t0 < t1) {
+    const int32_t* p = prog + task_off[t0];
+    const int b = st.g & 1;
+    tc::mbar_expect_tx(&st.tma_bar[b], S::B_BYTES);
+    tc::bulk_g2s(sB + b * S::B_BYTES, Btiles + (size_t)p[3] * S::B_BYTES, S::B_BYTES, &st.tma_bar[b]);
+    st.tma_issued = st.g + 1;
+  }
+  int pend_g = -1, pend_q1 = 0, pend_slots = 0, pend_acc = 0;
+  for (int t = t0; t < t1 && !st.failed; ++t) {
     const int32_t* p = prog + task_off[t];
-    const double* pw = progw + task_w[t];
     const int q1b = __ldg(p), nslots = __ldg(p + 1), nchan = __ldg(p + 2);
     p += 3;
     const int acc = (t - t0) & 1;
     // another CTA's bounded wait gave up: stop early (uniform: every thread reads the word)
     if (__syncthreads_or(*(volatile int*)status != 0)) {
-      failed = 1;
+      st.failed = 1;
       break;
     }
     for (int ci = 0; ci < nchan; ++ci) {
-      const int sc = __ldg(p);
+      int gs = __ldg(p + 1);
       int ngs[4];
 #pragma unroll
-      for (int s = 0; s < 4; ++s) ngs[s] = s < nslots ? __ldg(p + 1 + s) : 0;
-      p += 1 + nslots;
+      for (int s = 0; s < 4; ++s) ngs[s] = s < nslots ? __ldg(p + 2 + s) : 0;
+      p += 2 + nslots;
+      const int g = st.g;
       const int buf = g & 1;  // B tile buffer and MMA barrier of this channel
       for (int s = 0; s < nslots; ++s) {
-        if (!active) {
-          for (int gi = 0; gi < ngs[s]; ++gi) {
-            const int ne = __ldg(p) >> 16;
-            p += 1 + ne;
-            pw += ne;
-          }
-          continue;
-        }
+        const int g0 = gs;
+        gs += ngs[s];
+        if (!active) continue;
         double Phi[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) Phi[k] = 0.0;
-        for (int gi = 0; gi < ngs[s]; ++gi) {
-          const int hdr = __ldg(p);
-          const int q2 = hdr & 0xffff, ne = hdr >> 16;
-          ++p;
-          double h = 0.0;
-          for (int e = 0; e < ne; ++e) h = fma(__ldg(pw + e), __ldg(ft + (__ldg(p + e) * K + k3) * 32), h);
-          p += ne;
-          pw += ne;
-          const double* f2 = ft + q2 * K * 32;
-          double fv[K];
-#pragma unroll
-          for (int k2 = 0; k2 < K; ++k2) fv[k2] = __ldg(f2 + k2 * 32);
-#pragma unroll
-          for (int k2 = 0; k2 < K; ++k2) Phi[k2] = fma(fv[k2], h, Phi[k2]);
-        }
+        phi_slice<K>(Phi, groups, gw, g0, ngs[s], ft, k3);
         if (s == 0 && g >= 1) {
           // the single A tile is read by MMA(g-1): wait for it before the first write
-          if (!tc::mbar_wait(&mma_bar[(g - 1) & 1], ((g - 1) >> 1) & 1)) failed = 1;
+          if (!tc::mbar_wait(&st.mma_bar[(g - 1) & 1], ((g - 1) >> 1) & 1)) st.failed = 1;
         }
         const int row = s * 32 + lane;
 #pragma unroll
         for (int k2 = 0; k2 < K; ++k2) {
-          const uint32_t off = a_offset(row, k2 * K + k3, S::ESZ, S::SBO_A);
+          const uint32_t off = a_offset(row, k2 * K + k3, S::ESZ, S::SBO);
           if constexpr (TF32) {
-            float v;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(*(uint32_t*)&v) : "f"((float)Phi[k2]));
-            *(float*)(sA + off) = v;
+            *(uint32_t*)(sA + off) = d2f_bits<10>(Phi[k2]);
           } else {
-            *(__nv_bfloat16*)(sA + off) = __double2bfloat16(Phi[k2]);
+            *(uint16_t*)(sA + off) = (uint16_t)(d2f_bits<7>(Phi[k2]) >> 16);
           }
         }
       }
-      // epilogue of the previous task (warps 0-3), once its last MMA has completed
-      if (ci == 0 && pend_g >= 0 && k3 < 4) {
-        if (!tc::mbar_wait(&mma_bar[pend_g & 1], (pend_g >> 1) & 1)) failed = 1;
-        tc::tc_fence_after();
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(32 * k3) << 16) + pend_acc * S::NN, v);
-        const int q1 = pend_q1 + k3;
-        if (k3 < pend_task_slots && cell < ncells) {
-#pragma unroll
-          for (int k1 = 0; k1 < K && k1 < 16; ++k1) {
-            double val = (double)v[k1];
-            if ((k1 == 0 && q1 < 4) || (k1 == 1 && q1 == 0)) val = 0.0;
-            qout[cell * (int64_t)K * NQ + (int64_t)k1 * NQ + q1] = val;
-          }
-        }
-        if constexpr (S::NN > 16) {
-          tc::tmem_ld16(tmem + ((uint32_t)(32 * k3) << 16) + pend_acc * S::NN + 16, v);
-          if (k3 < pend_task_slots && cell < ncells) {
-#pragma unroll
-            for (int k1 = 16; k1 < K; ++k1) qout[cell * (int64_t)K * NQ + (int64_t)k1 * NQ + q1] = (double)v[k1 - 16];
-          }
-        }
-        tc::tc_fence_before();
+      if (ci == 0 && pend_g >= 0) {
+        tc_epilogue<K, TF32>(st, pend_g, pend_acc, pend_q1, pend_slots, qout, cell, ncells, NQ);
+        pend_g = -1;
       }
-      if (ci == 0) pend_g = -1;
       tc::fence_proxy_async();
-      failed = __syncthreads_or(failed);
-      if (failed) break;
+      st.failed = __syncthreads_or(st.failed);
+      if (st.failed) break;
       if (tid == 0) {
         tc::tc_fence_after();
-        const bool tma_ok = tc::mbar_wait(&tma_bar[buf], (g >> 1) & 1);
-        if (tma_ok) tma_waited = g + 1;
+        const bool tma_ok = tc::mbar_wait(&st.tma_bar[buf], (g >> 1) & 1);
+        if (tma_ok) st.tma_waited = g + 1;
         if (!tma_ok) {
           atomicExch(status, 1);
         } else {
-          const uint32_t d = tmem + acc * S::NN;
+          const uint32_t d = st.tmem + acc * S::NN;
 #pragma unroll 1
-          for (int st = 0; st < S::NSTEP; ++st) {
-            const uint64_t ad = tc::smem_desc(sA_u + st * 256, 128, S::SBO_A);
-            const uint64_t bd = tc::smem_desc(sB_u + buf * S::B_BYTES + st * 256, 128, S::SBO_A);
-            tc::mma<TF32>(d, ad, bd, idesc, (ci > 0 || st > 0) ? 1u : 0u);
+          for (int k = 0; k < S::NSTEP; ++k) {
+            const uint64_t ad = tc::smem_desc(sA_u + k * 256, 128, S::SBO);
+            const uint64_t bd = tc::smem_desc(sB_u + buf * S::B_BYTES + k * 256, 128, S::SBO);
+            tc::mma<TF32>(d, ad, bd, idesc, (ci > 0 || k > 0) ? 1u : 0u);
           }
-          tc::mma_commit(&mma_bar[buf]);
-          // prefetch the B tile of the next channel into the other buffer once MMA(g-1) released it
+          tc::mma_commit(&st.mma_bar[buf]);
+          // prefetch the next channel's B tile into the other buffer once MMA(g-1) released it
           int nsc = -1;
           if (ci + 1 < nchan) {
             nsc = __ldg(p);
           } else if (t + 1 < t1) {
-            const int32_t* pn = prog + task_off[t + 1];
-            if (pn[2] > 0) nsc = pn[3];
+            nsc = prog[task_off[t + 1] + 3];
           }
           if (nsc >= 0) {
-            bool ok = true;
-            if (g >= 1) ok = tc::mbar_wait(&mma_bar[(g - 1) & 1], ((g - 1) >> 1) & 1);
+            const bool ok = g < 1 || tc::mbar_wait(&st.mma_bar[(g - 1) & 1], ((g - 1) >> 1) & 1);
             if (!ok) {
               atomicExch(status, 1);
             } else {
-              tc::mbar_expect_tx(&tma_bar[buf ^ 1], S::B_BYTES);
-              tc::bulk_g2s(sB + (buf ^ 1) * S::B_BYTES, Btiles + (size_t)nsc * S::B_BYTES, S::B_BYTES, &tma_bar[buf ^ 1]);
-              tma_issued = g + 2;
+              tc::mbar_expect_tx(&st.tma_bar[buf ^ 1], S::B_BYTES);
+              tc::bulk_g2s(sB + (buf ^ 1) * S::B_BYTES, Btiles + (size_t)nsc * S::B_BYTES, S::B_BYTES,
+                           &st.tma_bar[buf ^ 1]);
+              st.tma_issued = g + 2;
             }
           }
         }
       }
-      ++g;
+      st.g = g + 1;
     }
-    pend_g = g - 1;
+    pend_g = st.g - 1;
     pend_q1 = q1b;
-    pend_task_slots = nslots;
+    pend_slots = nslots;
     pend_acc = acc;
   }
-  // epilogue of the last task
-  if (!failed && pend_g >= 0 && k3 < 4) {
-    if (tc::mbar_wait(&mma_bar[pend_g & 1], (pend_g >> 1) & 1)) {
-      tc::tc_fence_after();
-      float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(32 * k3) << 16) + pend_acc * S::NN, v);
-      const int q1 = pend_q1 + k3;
-      if (k3 < pend_task_slots && cell < ncells) {
-#pragma unroll
-        for (int k1 = 0; k1 < K && k1 < 16; ++k1) {
-          double val = (double)v[k1];
-          if ((k1 == 0 && q1 < 4) || (k1 == 1 && q1 == 0)) val = 0.0;
-          qout[cell * (int64_t)K * NQ + (int64_t)k1 * NQ + q1] = val;
-        }
-      }
-      if constexpr (S::NN > 16) {
-        tc::tmem_ld16(tmem + ((uint32_t)(32 * k3) << 16) + pend_acc * S::NN + 16, v);
-        if (k3 < pend_task_slots && cell < ncells) {
-#pragma unroll
-          for (int k1 = 16; k1 < K; ++k1) qout[cell * (int64_t)K * NQ + (int64_t)k1 * NQ + q1] = (double)v[k1 - 16];
-        }
-      }
-    } else {
-      failed = 1;
+  if (!st.failed && pend_g >= 0) tc_epilogue<K, TF32>(st, pend_g, pend_acc, pend_q1, pend_slots, qout, cell, ncells, NQ);
+  st.failed = __syncthreads_or(st.failed);
+}
+
+template <int K, bool TF32>
+__global__ void __launch_bounds__(32 * tc_warps<K>(), 1)
+    tc_kernel(const double* __restrict__ ftile, double* __restrict__ qout, int64_t ncells, int NQ,
+              const int32_t* __restrict__ prog, const int4* __restrict__ groups, const double2* __restrict__ gw,
+              const int32_t* __restrict__ task_off, const int32_t* __restrict__ chunks,
+              const uint8_t* __restrict__ Btiles, int* __restrict__ status) {
+  using S = TcShape<K, TF32>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  TcState st;
+  tc_setup(st, smem, S::TMEM_COLS);
+  const int64_t tile = blockIdx.x;
+  const int t0 = chunks[blockIdx.y], t1 = chunks[blockIdx.y + 1];
+  run_tile<K, TF32>(st, ftile + tile * (int64_t)NQ * K * 32, qout, tile * 32 + (threadIdx.x & 31), ncells, NQ, prog,
+                    groups, gw, task_off, t0, t1, Btiles, status);
+  tc_teardown(st, S::TMEM_COLS, status);
+}
+
+// Ragged persistent kernel: CTAs pull work items (shape, tile, task range) from a
+// device queue until it is empty.  Blocks are as wide as the largest K in the batch.
+template <bool TF32>
+__global__ void __launch_bounds__(32 * 17, 1)
+    ragged_tc_kernel(const RaggedShape* __restrict__ shapes, const RaggedItem* __restrict__ items, int nitems,
+                     int* __restrict__ queue, const double* __restrict__ ftile, double* __restrict__ qout,
+                     int tmem_cols, int* __restrict__ status) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ int item_s;
+  TcState st;
+  tc_setup(st, smem, tmem_cols);
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(queue, 1);
+    __syncthreads();
+    const int it = item_s;
+    __syncthreads();
+    if (it >= nitems || st.failed) break;
+    const RaggedItem I = items[it];
+    const RaggedShape& S = shapes[I.shape];
+    const int64_t cell = (int64_t)I.tile * 32 + (threadIdx.x & 31);
+    const double* ft = ftile + S.ftile_off + (int64_t)I.tile * S.NQ * S.K * 32;
+    double* q = qout + S.q_off;
+#define WEF_RAGGED_CASE(k)                                                                                      \
+  case k:                                                                                                       \
+    run_tile<k, TF32>(st, ft, q, cell, S.ncells, S.NQ, S.prog, S.groups, S.gw, S.task_off, I.t0, I.t1,            \
+                      TF32 ? S.Btf32 : S.Bbf16, status);                                                        \
+    break;
+    switch (S.K) {
+      WEF_RAGGED_CASE(2) WEF_RAGGED_CASE(3) WEF_RAGGED_CASE(4) WEF_RAGGED_CASE(5) WEF_RAGGED_CASE(6)
+      WEF_RAGGED_CASE(7) WEF_RAGGED_CASE(8) WEF_RAGGED_CASE(9) WEF_RAGGED_CASE(10) WEF_RAGGED_CASE(11)
+      WEF_RAGGED_CASE(12) WEF_RAGGED_CASE(13) WEF_RAGGED_CASE(14) WEF_RAGGED_CASE(15) WEF_RAGGED_CASE(16)
+      WEF_RAGGED_CASE(17)
+      default:
+        st.failed = 1;
     }
+#undef WEF_RAGGED_CASE
   }
-  if (failed && tid == 0) atomicExch(status, 1);
-  // drain: wait (bounded) for outstanding MMAs and bulk copies before releasing TMEM
-  if (tid == 0 && g >= 1) {
-    tc::mbar_wait(&mma_bar[(g - 1) & 1], ((g - 1) >> 1) & 1);
-  }
-  if (tid == 0 && tma_issued > tma_waited) {
-    // a bulk copy for channel tma_issued - 1 is still in flight (only after a failure)
-    const int gp = tma_issued - 1;
-    tc::mbar_wait(&tma_bar[gp & 1], (gp >> 1) & 1);
-  }
-  tc::tc_fence_before();
-  __syncthreads();
-  if (k3 == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
+  tc_teardown(st, tmem_cols, status);
 }
 
 template <int K, bool TF32>
@@ -288,9 +350,14 @@ cudaError_t launch_tc_k(const double* ftile, double* q, int64_t ncells, int NQ, 
     attr = true;
   }
   dim3 grid((unsigned)ntiles, (unsigned)nchunks);
-  tc_kernel<K, TF32><<<grid, 32 * tc_warps<K>(), S::SMEM, s>>>(ftile, q, ncells, NQ, p.prog, p.progw, p.task_off, p.task_w, chunks,
-                                                  Btiles, status);
+  tc_kernel<K, TF32><<<grid, 32 * tc_warps<K>(), S::SMEM, s>>>(ftile, q, ncells, NQ, p.prog, p.groups, p.gw,
+                                                              p.task_off, chunks, Btiles, status);
   return cudaGetLastError();
+}
+
+template <int K>
+int smem_for(bool tf32) {
+  return tf32 ? TcShape<K, true>::SMEM : TcShape<K, false>::SMEM;
 }
 
 }  // namespace
@@ -300,6 +367,19 @@ int tc_b_tile_bytes(int K, bool tf32) {
   const int kp = (K * K + kstep - 1) / kstep * kstep;
   const int nn = K <= 16 ? 16 : 32;
   return nn * kp * esz;
+}
+
+int tc_smem_bytes(int K, bool tf32) {
+  switch (K) {
+#define WEF_S(k) \
+  case k:        \
+    return smem_for<k>(tf32);
+    WEF_S(2) WEF_S(3) WEF_S(4) WEF_S(5) WEF_S(6) WEF_S(7) WEF_S(8) WEF_S(9) WEF_S(10) WEF_S(11) WEF_S(12) WEF_S(13)
+    WEF_S(14) WEF_S(15) WEF_S(16) WEF_S(17)
+#undef WEF_S
+    default:
+      return 0;
+  }
 }
 
 // Host-side layout of one symmetrised core tile as the MMA's B operand:
@@ -342,6 +422,41 @@ cudaError_t launch_tc(int K, bool tf32, const double* ftile, double* q, int64_t 
       return cudaErrorInvalidValue;
   }
 #undef WEF_TC_CASE
+}
+
+cudaError_t prepare_ragged_tc() {
+  // the largest dynamic size any shape needs (K = 17, TF32), within the opt-in limit
+  // left after the kernel's static shared memory
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  for (int tf = 0; tf < 2 && e == cudaSuccess; ++tf) {
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, tf ? (const void*)ragged_tc_kernel<true> : (const void*)ragged_tc_kernel<false>);
+    if (e != cudaSuccess) break;
+    int need = 0;
+    for (int k = 2; k <= 17; ++k) need = need > tc_smem_bytes(k, tf != 0) ? need : tc_smem_bytes(k, tf != 0);
+    const int allowed = optin - (int)fa.sharedSizeBytes;
+    if (need > allowed) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(tf ? (const void*)ragged_tc_kernel<true> : (const void*)ragged_tc_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+  }
+  return e;
+}
+
+cudaError_t launch_ragged_tc(bool tf32, int max_k, int nsm, const RaggedShape* shapes, const RaggedItem* items,
+                             int nitems, int* queue, const double* ftile, double* q, int* status, cudaStream_t s) {
+  int smem = 0, tmem_cols = 32;
+  for (int k = 2; k <= max_k; ++k) smem = smem > tc_smem_bytes(k, tf32) ? smem : tc_smem_bytes(k, tf32);
+  if (max_k > 16) tmem_cols = 64;
+  const int warps = max_k < 4 ? 4 : max_k;
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  if (tf32)
+    ragged_tc_kernel<true><<<nsm, 32 * warps, smem, s>>>(shapes, items, nitems, queue, ftile, q, tmem_cols, status);
+  else
+    ragged_tc_kernel<false><<<nsm, 32 * warps, smem, s>>>(shapes, items, nitems, queue, ftile, q, tmem_cols, status);
+  return cudaGetLastError();
 }
 
 }  // namespace wef

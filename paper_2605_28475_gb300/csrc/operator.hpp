@@ -1,0 +1,55 @@
+// The operator object behind the opaque wef_op handle (shared by the C ABI files).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "tables.hpp"
+
+using wef::Channel;
+using wef::Program;
+using wef::Tables;
+
+struct wef_operator {
+  Tables T;
+  double gamma = 0.0;
+  int device = 0;
+  int sms = 1;
+  // programs: [0] one q1 per task (FP64 path), [1] four q1 per task (tensor-core path)
+  struct DevProg {
+    int32_t *prog = nullptr, *off = nullptr, *chunks = nullptr, *groups = nullptr;
+    double* gw = nullptr;
+    std::vector<int> chunk_n, chunk_pos;  // chunk counts available and their offsets in `chunks`
+  } dp[2];
+  int* d_status = nullptr;  // set by kernels whose bounded waits gave up
+  // core
+  double* d_R64 = nullptr;      // symmetrised core [sc][k3][k1][k2]
+  uint8_t* d_Bbf16 = nullptr;   // packed MMA B tiles, BF16
+  uint8_t* d_Btf32 = nullptr;   // packed MMA B tiles, TF32
+  bool has_core = false;
+  // tracing
+  cudaEvent_t trace_start = nullptr, trace_stop = nullptr;
+
+  void release_core() {
+    cudaFree(d_R64);
+    cudaFree(d_Bbf16);
+    cudaFree(d_Btf32);
+    d_R64 = nullptr;
+    d_Bbf16 = d_Btf32 = nullptr;
+    has_core = false;
+  }
+  void release() {
+    for (auto& d : dp) {
+      cudaFree(d.prog);
+      cudaFree(d.off);
+      cudaFree(d.groups);
+      cudaFree(d.chunks);
+      cudaFree(d.gw);
+      d = DevProg();
+    }
+    cudaFree(d_status);
+    d_status = nullptr;
+    release_core();
+  }
+};

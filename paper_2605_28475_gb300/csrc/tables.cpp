@@ -130,11 +130,10 @@ struct Entry {
   double w;
 };
 
-// Append one task to a program.  slices[s] = list of per-channel entry lists.
-void emit_task(Program& P, int q1_base, int nslots, int l1, const std::vector<int>& chans,
-               const std::vector<std::vector<std::vector<Entry>>>& ent /* [chan][slot] */, int K, bool radial_fp64) {
+// Append one task to a program.  ent[chan][slot] = that slice's entries sorted by (q2, q3).
+std::string emit_task(Program& P, int q1_base, int nslots, int l1, const std::vector<int>& chans,
+                      const std::vector<std::vector<std::vector<Entry>>>& ent, int K, bool radial_fp64) {
   P.task_off.push_back((int32_t)P.prog.size());
-  P.task_w.push_back((int32_t)P.progw.size());
   P.task_l1.push_back(l1);
   P.prog.push_back(q1_base);
   P.prog.push_back(nslots);
@@ -142,7 +141,8 @@ void emit_task(Program& P, int q1_base, int nslots, int l1, const std::vector<in
   double cost = 0.0;
   for (size_t ci = 0; ci < chans.size(); ++ci) {
     P.prog.push_back(chans[ci]);
-    size_t hdr = P.prog.size();
+    P.prog.push_back((int32_t)(P.groups.size() / 4));
+    const size_t hdr = P.prog.size();
     for (int s = 0; s < nslots; ++s) P.prog.push_back(0);
     for (int s = 0; s < nslots; ++s) {
       const auto& e = ent[ci][s];
@@ -152,11 +152,13 @@ void emit_task(Program& P, int q1_base, int nslots, int l1, const std::vector<in
         size_t j = i;
         while (j < e.size() && e[j].q2 == e[i].q2) ++j;
         const int ne = (int)(j - i);
-        P.prog.push_back(e[i].q2 | (ne << 16));
-        for (size_t k = i; k < j; ++k) {
-          P.prog.push_back(e[k].q3);
-          P.progw.push_back(e[k].w);
-        }
+        if (ne > 2) return "a rank-1 group with more than two entries";
+        P.groups.push_back(e[i].q2);
+        P.groups.push_back(ne);
+        P.groups.push_back(e[i].q3);
+        P.groups.push_back(ne > 1 ? e[i + 1].q3 : e[i].q3);
+        P.gw.push_back(e[i].w);
+        P.gw.push_back(ne > 1 ? e[i + 1].w : 0.0);
         cost += 2.0 * K * K + 2.0 * K * ne;
         ++ng;
         i = j;
@@ -166,9 +168,31 @@ void emit_task(Program& P, int q1_base, int nslots, int l1, const std::vector<in
     }
   }
   P.task_cost.push_back(cost);
+  return "";
 }
 
 }  // namespace
+
+// Split tasks [0, ntasks) into n contiguous chunks of about equal cost.
+std::vector<int32_t> split_tasks(const std::vector<double>& cost, int n) {
+  const int nt = (int)cost.size();
+  n = std::max(1, std::min(n, nt));
+  double total = 0.0;
+  for (double c : cost) total += c;
+  std::vector<int32_t> b(1, 0);
+  double acc = 0.0;
+  int t = 0;
+  for (int i = 1; i < n; ++i) {
+    const double target = total * i / n;
+    while (t < nt && acc + 0.5 * cost[t] < target) acc += cost[t++];
+    if (t <= b.back()) t = b.back() + 1;
+    if (t > nt - (n - i)) t = nt - (n - i);
+    b.push_back(t);
+  }
+  b.push_back(nt);
+  return b;
+}
+
 
 std::string build_tables(int kmax, int lmax, Tables& t) {
   if (kmax < 0 || kmax > 16 || lmax < 0 || lmax > 20) return "Kmax must be in [0, 16] and Lmax in [0, 20]";
@@ -257,11 +281,11 @@ std::string build_tables(int kmax, int lmax, Tables& t) {
         std::vector<std::vector<std::vector<Entry>>> ent(chans.size(), std::vector<std::vector<Entry>>(ns));
         for (size_t ci = 0; ci < chans.size(); ++ci)
           for (int s = 0; s < ns; ++s) ent[ci][s] = sl[(size_t)chans[ci] * t.NQ + q1b + s];
-        emit_task(P, q1b, ns, l1, chans, ent, t.K, variant == 0);
+        std::string err = emit_task(P, q1b, ns, l1, chans, ent, t.K, variant == 0);
+        if (!err.empty()) return err;
       }
     }
     P.task_off.push_back((int32_t)P.prog.size());
-    P.task_w.push_back((int32_t)P.progw.size());
   }
   return "";
 }

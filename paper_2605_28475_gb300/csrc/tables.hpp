@@ -21,20 +21,20 @@ double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3);
 double real_gaunt(int l1, int m1, int l2, int m2, int l3, int m3);
 
 // One evaluation "program": the instruction stream that the kernels walk.
-// Tasks are groups of output rows (cell x q1); each task lists its channels,
-// and per channel and per q1 slot the rank-1 groups (q2; entries (q3, w)).
+// Tasks are groups of output rows (cell x q1); each task lists its channels, and
+// per channel and per q1 slot a run of rank-1 groups.
 //
-// Layout of prog (int32 words), per task:
-//   [q1_base, nslots, nchan]
-//   per channel: [sc, ngroups_slot0, ..., ngroups_slot{nslots-1}]
-//     per slot, per group: [q2 | ne << 16], then ne words q3
-// Weights are consumed in stream order from progw, starting at task_w[t].
+// prog (int32 words), per task: [q1_base, nslots, nchan], then per channel
+//   [sc, gstart, ngroups_slot0, ..., ngroups_slot{nslots-1}]
+// where the slot groups are consecutive records of `groups` from index gstart.
+// groups: 4 int32 per group {q2, ne, q3a, q3b} (ne in {1, 2}; q3b = q3a if ne = 1);
+// gw: 2 doubles per group {weight a, weight b} (b = 0 if ne = 1).
 struct Program {
   int nslots = 1;
   std::vector<int32_t> prog;
-  std::vector<double> progw;
+  std::vector<int32_t> groups;
+  std::vector<double> gw;
   std::vector<int32_t> task_off;  // word offset of task t (size ntasks + 1)
-  std::vector<int32_t> task_w;    // weight offset of task t
   std::vector<double> task_cost;  // FP64 flops per cell of task t (for load balance)
   std::vector<int32_t> task_l1;
   int ntasks() const { return (int)task_cost.size(); }
@@ -53,6 +53,9 @@ struct Tables {
   Program prog4;  // up to four q1 of one shell per task (tensor-core path, 128-row tiles)
   int64_t n_sym_entries = 0, n_sym_groups = 0, n_sym_slices = 0;
 };
+
+// Split tasks [0, ntasks) into n contiguous chunks of about equal cost; returns n+1 bounds.
+std::vector<int32_t> split_tasks(const std::vector<double>& cost, int n);
 
 // Build everything; returns "" on success or an error message.
 std::string build_tables(int kmax, int lmax, Tables& t);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/wef.h"
+#include "operator.hpp"
 #include "wef_internal.hpp"
 
 using namespace wef;
@@ -35,70 +36,10 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
   return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-// Split tasks [0, ntasks) into n contiguous chunks of about equal cost.
-std::vector<int32_t> split_tasks(const std::vector<double>& cost, int n) {
-  const int nt = (int)cost.size();
-  n = std::max(1, std::min(n, nt));
-  double total = 0.0;
-  for (double c : cost) total += c;
-  std::vector<int32_t> b(1, 0);
-  double acc = 0.0;
-  int t = 0;
-  for (int i = 1; i < n; ++i) {
-    const double target = total * i / n;
-    while (t < nt && acc + 0.5 * cost[t] < target) acc += cost[t++];
-    if (t <= b.back()) t = b.back() + 1;
-    if (t > nt - (n - i)) t = nt - (n - i);
-    b.push_back(t);
-  }
-  b.push_back(nt);
-  return b;
-}
-
 }  // namespace
 
-struct wef_operator {
-  Tables T;
-  double gamma = 0.0;
-  int device = 0;
-  int sms = 1;
-  // programs: [0] one q1 per task (FP64 path), [1] four q1 per task (tensor-core path)
-  struct DevProg {
-    int32_t *prog = nullptr, *off = nullptr, *w = nullptr, *chunks = nullptr;
-    double* progw = nullptr;
-    std::vector<int> chunk_n, chunk_pos;  // chunk counts available and their offsets in `chunks`
-  } dp[2];
-  int* d_status = nullptr;  // set by kernels whose bounded waits gave up
-  // core
-  double* d_R64 = nullptr;      // symmetrised core [sc][k3][k1][k2]
-  uint8_t* d_Bbf16 = nullptr;   // packed MMA B tiles, BF16
-  uint8_t* d_Btf32 = nullptr;   // packed MMA B tiles, TF32
-  bool has_core = false;
-  // tracing
-  cudaEvent_t trace_start = nullptr, trace_stop = nullptr;
+wef_status wef::set_error(wef_status s, const std::string& msg) { return fail(s, msg); }
 
-  void release_core() {
-    cudaFree(d_R64);
-    cudaFree(d_Bbf16);
-    cudaFree(d_Btf32);
-    d_R64 = nullptr;
-    d_Bbf16 = d_Btf32 = nullptr;
-    has_core = false;
-  }
-  void release() {
-    for (auto& d : dp) {
-      cudaFree(d.prog);
-      cudaFree(d.off);
-      cudaFree(d.w);
-      cudaFree(d.chunks);
-      cudaFree(d.progw);
-      d = DevProg();
-    }
-    cudaFree(d_status);
-    d_status = nullptr;
-    release_core();
-  }
-};
 
 namespace {
 
@@ -113,9 +54,9 @@ cudaError_t ensure_device(wef_operator* op) {
     const Program& P = v == 0 ? op->T.prog1 : op->T.prog4;
     wef_operator::DevProg& D = op->dp[v];
     e = upload(&D.prog, P.prog);
-    if (e == cudaSuccess) e = upload(&D.progw, P.progw);
+    if (e == cudaSuccess) e = upload(&D.groups, P.groups);
+    if (e == cudaSuccess) e = upload(&D.gw, P.gw);
     if (e == cudaSuccess) e = upload(&D.off, P.task_off);
-    if (e == cudaSuccess) e = upload(&D.w, P.task_w);
     if (e == cudaSuccess) {
       std::vector<int32_t> all;
       D.chunk_n.clear();
@@ -279,7 +220,7 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
   int idx = 0;
   while (idx + 1 < (int)D.chunk_n.size() && ntiles * D.chunk_n[idx] < want) ++idx;
   const Program& P = v == 0 ? op->T.prog1 : op->T.prog4;
-  DevProgram p{D.prog, D.progw, D.off, D.w, P.ntasks()};
+  DevProgram p{D.prog, (const int4*)D.groups, (const double2*)D.gw, D.off, P.ntasks()};
   if (op->trace_start) cudaEventRecord(op->trace_start, s);
   if (prec == WEF_FP64)
     e = launch_fp64(K, ftile, q_dev, ncells, NQ, p, D.chunks + D.chunk_pos[idx], D.chunk_n[idx], op->d_R64, s);

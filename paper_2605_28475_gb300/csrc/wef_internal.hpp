@@ -6,15 +6,16 @@
 #include <string>
 
 #include "tables.hpp"
+#include "../../include/wef.h"
 
 namespace wef {
 
 // Device copy of one Program (see tables.hpp).
 struct DevProgram {
   const int32_t* prog = nullptr;
-  const double* progw = nullptr;
+  const int4* groups = nullptr;
+  const double2* gw = nullptr;
   const int32_t* task_off = nullptr;
-  const int32_t* task_w = nullptr;
   int ntasks = 0;
 };
 
@@ -36,6 +37,44 @@ void tc_pack_b_tile(int K, bool tf32, const double* Rt /* [k1][k2][k3] */, uint8
 // status: device int set to 1 if a bounded wait inside the kernel gave up.
 cudaError_t launch_tc(int K, bool tf32, const double* ftile, double* q, int64_t ncells, int NQ, const DevProgram& p,
                       const int32_t* chunks, int nchunks, const uint8_t* Btiles, int* status, cudaStream_t s);
+
+// One shape (operator) of a ragged batch, as the persistent kernel sees it.
+// Offsets are in doubles from the bases passed to the kernels.
+struct RaggedShape {
+  int K, NQ;
+  int64_t ncells;
+  int64_t tile0;      // first tile of this shape in the batch's tile numbering
+  int64_t f_off;      // first cell of this shape in f and Q
+  int64_t ftile_off;  // this shape's re-tiled region in the workspace
+  const int32_t* prog;
+  const int4* groups;
+  const double2* gw;
+  const int32_t* task_off;
+  const uint8_t* Bbf16;
+  const uint8_t* Btf32;
+  int64_t q_off;      // == f_off (same layout for Q)
+};
+
+// One work item: tasks [t0, t1) of tile `tile` of shape `shape`.
+struct RaggedItem {
+  int shape, tile, t0, t1;
+};
+
+int tc_smem_bytes(int K, bool tf32);
+
+// Re-tile every shape's cells: grid over all tiles of the batch.
+cudaError_t launch_ragged_tile_f(const RaggedShape* shapes, int nshapes, int64_t total_tiles, int max_n,
+                                 const double* f, double* ftile, cudaStream_t s);
+
+// Raise the persistent kernel's shared-memory limit (call once, outside stream capture).
+cudaError_t prepare_ragged_tc();
+
+// Persistent ragged contraction: nsm CTAs pull items from *queue (reset here).
+cudaError_t launch_ragged_tc(bool tf32, int max_k, int nsm, const RaggedShape* shapes, const RaggedItem* items,
+                             int nitems, int* queue, const double* ftile, double* q, int* status, cudaStream_t s);
+
+// Record `msg` as this thread's last error (returned by wef_last_error) and return `s`.
+wef_status set_error(wef_status s, const std::string& msg);
 
 std::string core_build(const Tables& T, double gamma, int pad_rad, int pad_ang, double* R);
 
