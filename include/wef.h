@@ -180,6 +180,26 @@ wef_status wef_set_trace_events(wef_op op, void* ev_start, void* ev_stop);
  */
 wef_status wef_device_status(wef_op op, int reset);
 
+/*
+ * wef_evaluate_noalloc - the FP64 evaluation of wef_evaluate (prec = WEF_FP64)
+ * for callers that cannot allocate device memory when they evaluate: it takes no
+ * workspace and allocates nothing, using instead a fixed scratch array of
+ * WEF_NOALLOC_SCRATCH_BYTES that the library keeps in device memory on every GPU
+ * that loads it, until the process exits.  The paper has no counterpart; this is
+ * a deployment convenience.
+ *   - Size limit: ncells * K * NQ * 8 bytes, rounded up to whole 32-cell tiles,
+ *     must fit the scratch (928 cells at Kmax = Lmax = 12); larger batches are
+ *     rejected with WEF_EINVAL and a message giving the limit.
+ *   - The first call on each device looks up the scratch's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls on a device share the one scratch array, which keeps the last
+ *     call's contents: calls that overlap on the GPU (other streams, other
+ *     threads) race and must be ordered by the caller.
+ *   - Same arguments, results and errors as wef_evaluate otherwise.
+ */
+#define WEF_NOALLOC_SCRATCH_BYTES (16u << 20)
+wef_status wef_evaluate_noalloc(wef_op op, const double* f_dev, double* q_dev, int64_t ncells, void* stream);
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* wef_last_error(void);
 

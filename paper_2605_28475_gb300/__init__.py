@@ -55,6 +55,7 @@ def lib():
             "wef_plan_autotune": ([vp, vp, vp, vp, i64, vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "wef_plan_status": ([vp, ctypes.c_int], ctypes.c_int),
             "wef_plan_destroy": ([vp], ctypes.c_int),
+            "wef_evaluate_noalloc": ([vp, vp, vp, i64, vp], ctypes.c_int),
             "wef_last_error": ([], ctypes.c_char_p),
             "wef_destroy": ([vp], ctypes.c_int),
         }
@@ -109,6 +110,10 @@ def wef_workspace_size(op, ncells, prec=WEF_FP64):
 
 def wef_evaluate(op, f_ptr, q_ptr, ncells, prec, ws_ptr, ws_bytes, stream_ptr):
     _check(lib().wef_evaluate(op, f_ptr, q_ptr, int(ncells), int(prec), ws_ptr, int(ws_bytes), stream_ptr))
+
+
+def wef_evaluate_noalloc(op, f_ptr, q_ptr, ncells, stream_ptr):
+    _check(lib().wef_evaluate_noalloc(op, f_ptr, q_ptr, int(ncells), stream_ptr))
 
 
 def wef_core_build(op, pad_rad=20, pad_ang=20):
