@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="tf32", choices=["fp64", "bf16", "tf32"])
+    ap.add_argument("--precision", default="tf32", choices=["fp64", "bf16", "tf32", "rf32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ncells", type=int, default=NCELLS)
     ap.add_argument("--cpu-sample-rows", type=int, default=384)
@@ -403,7 +403,7 @@ def main():
         return out
 
     variants = {}
-    order = [p for p in ("fp64", "bf16", "tf32") if p != args.precision] + [args.precision]
+    order = [p for p in ("fp64", "bf16", "tf32", "rf32") if p != args.precision] + [args.precision]
     for pr in order:
         variants[pr] = measure(pr, with_clocks=(pr == args.precision))
     head = variants[args.precision]

@@ -56,7 +56,9 @@ typedef enum {
 typedef enum {
   WEF_FP64 = 0,       /* everything in FP64 (angular coupling and radial contraction) */
   WEF_MIXED_BF16 = 1, /* FP64 angular coupling, BF16 x BF16 -> FP32 radial stage on tcgen05 */
-  WEF_MIXED_TF32 = 2  /* FP64 angular coupling, TF32 x TF32 -> FP32 radial stage on tcgen05 */
+  WEF_MIXED_TF32 = 2, /* FP64 angular coupling, TF32 x TF32 -> FP32 radial stage on tcgen05 */
+  WEF_RADIAL_FP32 = 3 /* radial-first ordering: both radial contractions in FP32 on the CUDA cores,
+                         Gaunt-weighted angular reduction in FP64 (Sec. 4.5.3 made dense) */
 } wef_precision;
 
 /* Flags of wef_upload_core. */
@@ -159,7 +161,9 @@ wef_status wef_core_build(wef_op op, int pad_rad, int pad_ang, double* R_out, in
  * wef_flops - arithmetic the evaluation executes per cell: FP64 flops (angular
  * coupling, plus the radial contraction for WEF_FP64) and tensor-core flops
  * (radial contraction, padded MMA shapes, for the mixed precisions).  An FMA
- * counts as 2.  Derived from the operator's programs; any out pointer may be NULL.
+ * counts as 2.  For WEF_RADIAL_FP32 the second output is the FP32 CUDA-core work of
+ * the two radial contractions instead.  Derived from the operator's programs; any
+ * out pointer may be NULL.
  */
 wef_status wef_flops(wef_op op, wef_precision prec, double* fp64_flops_per_cell, double* tc_flops_per_cell);
 

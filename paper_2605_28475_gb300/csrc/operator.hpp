@@ -23,10 +23,14 @@ struct wef_operator {
     std::vector<int> chunk_n, chunk_pos;  // chunk counts available and their offsets in `chunks`
   } dp[2];
   int* d_status = nullptr;  // set by kernels whose bounded waits gave up
+  // radial-first program
+  int32_t *r_tasks = nullptr, *r_chans = nullptr, *r_m3s = nullptr, *r_pairs = nullptr, *r_order = nullptr;
+  double* r_pw = nullptr;
   // core
   double* d_R64 = nullptr;      // symmetrised core [sc][k3][k1][k2]
   uint8_t* d_Bbf16 = nullptr;   // packed MMA B tiles, BF16
   uint8_t* d_Btf32 = nullptr;   // packed MMA B tiles, TF32
+  float* d_R32 = nullptr;       // symmetrised core, FP32 [sc][k1][k2][k3] (radial-first path)
   bool has_core = false;
   // tracing
   cudaEvent_t trace_start = nullptr, trace_stop = nullptr;
@@ -35,6 +39,8 @@ struct wef_operator {
     cudaFree(d_R64);
     cudaFree(d_Bbf16);
     cudaFree(d_Btf32);
+    cudaFree(d_R32);
+    d_R32 = nullptr;
     d_R64 = nullptr;
     d_Bbf16 = d_Btf32 = nullptr;
     has_core = false;
@@ -50,6 +56,12 @@ struct wef_operator {
     }
     cudaFree(d_status);
     d_status = nullptr;
+    for (int32_t** pp : {&r_tasks, &r_chans, &r_m3s, &r_pairs, &r_order}) {
+      cudaFree(*pp);
+      *pp = nullptr;
+    }
+    cudaFree(r_pw);
+    r_pw = nullptr;
     release_core();
   }
 };

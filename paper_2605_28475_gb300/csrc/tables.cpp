@@ -265,6 +265,57 @@ std::string build_tables(int kmax, int lmax, Tables& t) {
     for (size_t i = 0; i < v.size(); ++i)
       if (i == 0 || v[i].q2 != v[i - 1].q2) ++t.n_sym_groups;
   }
+  // Radial-first program: per shell, per channel, group the channel's entries by q3,
+  // then by q2; each (q2, q3) pair feeds at most two q1 of the shell.
+  {
+    RadialProgram& RP = t.rprog;
+    RP = RadialProgram();
+    const int K = t.K;
+    for (int l1 = 0; l1 <= lmax; ++l1) {
+      const int q1b = l1 * l1, n1 = 2 * l1 + 1;
+      RP.n1max = std::max(RP.n1max, n1);
+      const int cs = (int)RP.chans.size() / 4;
+      int nch = 0;
+      double cost = 0.0;
+      for (int sc = 0; sc < NS; ++sc) {
+        if (t.chans[t.sym_chan[sc]].l1 != l1) continue;
+        // (q3, q2) -> list of (q1 offset, w)
+        std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> byp;
+        for (int m = 0; m < n1; ++m)
+          for (const Entry& e : sl[(size_t)sc * t.NQ + q1b + m]) byp[{e.q3, e.q2}].push_back({m, e.w});
+        if (byp.empty()) continue;
+        const int ms = (int)RP.m3s.size() / 4;
+        int nm3 = 0, cur_q3 = -1;
+        for (const auto& kv : byp) {
+          const int q3 = kv.first.first, q2 = kv.first.second;
+          if (q3 != cur_q3) {
+            RP.m3s.insert(RP.m3s.end(), {q3, (int32_t)(RP.pairs.size() / 4), 0, 0});
+            cur_q3 = q3;
+            ++nm3;
+            cost += 2.0 * K * K * K;
+          }
+          const auto& v = kv.second;
+          if (v.size() > 2) return "a radial-first pair feeding more than two q1";
+          RP.pairs.insert(RP.pairs.end(), {q2, (int32_t)v.size(), v[0].first, v.size() > 1 ? v[1].first : v[0].first});
+          RP.pw.push_back(v[0].second);
+          RP.pw.push_back(v.size() > 1 ? v[1].second : 0.0);
+          RP.m3s[RP.m3s.size() - 2] += 1;
+          cost += 2.0 * K * K + 2.0 * K * (double)v.size();
+          RP.fp32_flops += 2.0 * K * K;
+          RP.fp64_flops += 2.0 * K * (double)v.size();
+        }
+        RP.fp32_flops += 2.0 * K * K * K * nm3;
+        RP.chans.insert(RP.chans.end(), {sc, ms, nm3, 0});
+        ++nch;
+      }
+      RP.tasks.insert(RP.tasks.end(), {q1b, n1, cs, nch});
+      RP.task_cost.push_back(cost);
+    }
+    RP.order.resize(RP.task_cost.size());
+    for (size_t i = 0; i < RP.order.size(); ++i) RP.order[i] = (int32_t)i;
+    std::stable_sort(RP.order.begin(), RP.order.end(),
+                     [&](int a, int b) { return RP.task_cost[a] > RP.task_cost[b]; });
+  }
   // Programs.
   for (int variant = 0; variant < 2; ++variant) {
     Program& P = variant == 0 ? t.prog1 : t.prog4;

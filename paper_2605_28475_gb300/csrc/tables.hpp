@@ -40,6 +40,22 @@ struct Program {
   int ntasks() const { return (int)task_cost.size(); }
 };
 
+// Radial-first program (SURVEY NEXT-1 ordering; paper Sec. 4.5.3 with a dense
+// two-stage radial contraction).  One task per output shell l1:
+//   tasks:  {q1_base, n1, chan_start, nchan}
+//   chans:  {sc, m3_start, n_m3, 0}        symmetrised channel and its q3 groups
+//   m3s:    {q3, pair_start, npairs, 0}    one group per q3 used by the channel
+//   pairs:  {q2, ne, q1a - q1_base, q1b - q1_base}, weights pw {ga, gb} (gb = 0 if ne = 1)
+// order:  task indices by decreasing cost (the persistent kernel's schedule).
+struct RadialProgram {
+  std::vector<int32_t> tasks, chans, m3s, pairs;
+  std::vector<double> pw;
+  std::vector<int32_t> order;
+  std::vector<double> task_cost;  // FP64 + FP32 flops per cell, for the schedule
+  double fp64_flops = 0.0, fp32_flops = 0.0;
+  int n1max = 1;
+};
+
 struct Tables {
   int kmax = 0, lmax = 0, K = 0, NQ = 0;
   std::vector<Channel> chans;        // paper order
@@ -51,6 +67,7 @@ struct Tables {
   std::vector<int> sym_chan, sym_partner;
   Program prog1;  // one q1 per task (FP64 path)
   Program prog4;  // up to four q1 of one shell per task (tensor-core path, 128-row tiles)
+  RadialProgram rprog;  // radial-first ordering
   int64_t n_sym_entries = 0, n_sym_groups = 0, n_sym_slices = 0;
 };
 

@@ -70,6 +70,13 @@ cudaError_t ensure_device(wef_operator* op) {
       e = upload(&D.chunks, all);
     }
   }
+  const RadialProgram& RP = op->T.rprog;
+  if (e == cudaSuccess) e = upload(&op->r_tasks, RP.tasks);
+  if (e == cudaSuccess) e = upload(&op->r_chans, RP.chans);
+  if (e == cudaSuccess) e = upload(&op->r_m3s, RP.m3s);
+  if (e == cudaSuccess) e = upload(&op->r_pairs, RP.pairs);
+  if (e == cudaSuccess) e = upload(&op->r_pw, RP.pw);
+  if (e == cudaSuccess) e = upload(&op->r_order, RP.order);
   if (e == cudaSuccess) e = cudaMalloc((void**)&op->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(op->d_status, 0, sizeof(int));
   if (e != cudaSuccess) op->release();
@@ -173,8 +180,16 @@ wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigne
       tc_pack_b_tile(K, true, Rt.data(), &Bt[(size_t)s * nt]);
     }
   }
+  // FP32 copy for the radial-first path, layout [sc][k1][k2][k3]
+  std::vector<float> R32((size_t)NS * K3);
+  for (int s = 0; s < NS; ++s)
+    for (int k1 = 0; k1 < K; ++k1)
+      for (int k2 = 0; k2 < K; ++k2)
+        for (int k3 = 0; k3 < K; ++k3)
+          R32[(((size_t)s * K + k1) * K + k2) * K + k3] = (float)R64[(((size_t)s * K + k3) * K + k1) * K + k2];
   op->release_core();
   cudaError_t e = upload(&op->d_R64, R64);
+  if (e == cudaSuccess) e = upload(&op->d_R32, R32);
   if (e == cudaSuccess) e = upload(&op->d_Bbf16, Bb);
   if (e == cudaSuccess) e = upload(&op->d_Btf32, Bt);
   if (e != cudaSuccess) {
@@ -187,9 +202,14 @@ wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigne
 
 wef_status wef_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int64_t* bytes) {
   if (!op || !bytes || ncells < 0) return fail(WEF_EINVAL, "wef_workspace_size: bad argument");
-  (void)prec;
   const int64_t ntiles = (ncells + 31) / 32;
-  *bytes = ntiles * 32 * (int64_t)op->T.K * op->T.NQ * (int64_t)sizeof(double);
+  const int64_t tile_elems = ntiles * 32 * (int64_t)op->T.K * op->T.NQ;
+  *bytes = tile_elems * (int64_t)sizeof(double);
+  if (prec == WEF_RADIAL_FP32 && ncells > 0) {
+    // queue word (256 bytes) + FP32 re-tiled f
+    const int64_t rb = 256 + (tile_elems * (int64_t)sizeof(float) + 255) / 256 * 256;
+    if (rb > *bytes) *bytes = rb;
+  }
   return WEF_OK;
 }
 
@@ -207,11 +227,22 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
   if (ncells > (int64_t)65535 * 32 * 1024) return fail(WEF_EINVAL, "wef_evaluate: ncells too large");
   cudaStream_t s = (cudaStream_t)stream;
   const int K = op->T.K, NQ = op->T.NQ;
+  if (prec == WEF_RADIAL_FP32) {
+    const RadialProgram& RP = op->T.rprog;
+    DevRadial r{(const int4*)op->r_tasks, (const int4*)op->r_chans, (const int4*)op->r_m3s, (const int4*)op->r_pairs,
+                (const double2*)op->r_pw, op->r_order, (int)RP.task_cost.size(), RP.n1max};
+    if (op->trace_start) cudaEventRecord(op->trace_start, s);
+    cudaError_t er = launch_rf(K, f_dev, (float*)((char*)workspace + 256), (int*)workspace, q_dev, ncells, NQ, r,
+                               op->d_R32, op->sms, s);
+    if (op->trace_stop) cudaEventRecord(op->trace_stop, s);
+    if (er != cudaSuccess) return cuda_fail(er, "wef_evaluate: radial-first kernels");
+    return WEF_OK;
+  }
   double* ftile = (double*)workspace;
   cudaError_t e = launch_tile_f(f_dev, ftile, ncells, K, NQ, s);
   if (e != cudaSuccess) return cuda_fail(e, "wef_evaluate: tile kernel");
   if (prec != WEF_FP64 && prec != WEF_MIXED_BF16 && prec != WEF_MIXED_TF32)
-    return fail(WEF_EINVAL, "wef_evaluate: unknown precision");
+    return fail(WEF_EINVAL, "wef_evaluate: unknown precision");  // (radial-first handled above)
   // chunk count: enough CTAs for several waves of the GPU
   const int v = prec == WEF_FP64 ? 0 : 1;
   const wef_operator::DevProg& D = op->dp[v];
@@ -244,6 +275,11 @@ wef_status wef_core_build(wef_op op, int pad_rad, int pad_ang, double* R_out, in
 
 wef_status wef_flops(wef_op op, wef_precision prec, double* fp64_flops_per_cell, double* tc_flops_per_cell) {
   if (!op) return fail(WEF_EINVAL, "wef_flops: op is NULL");
+  if (prec == WEF_RADIAL_FP32) {
+    if (fp64_flops_per_cell) *fp64_flops_per_cell = op->T.rprog.fp64_flops;
+    if (tc_flops_per_cell) *tc_flops_per_cell = op->T.rprog.fp32_flops;
+    return WEF_OK;
+  }
   const Program& P = prec == WEF_FP64 ? op->T.prog1 : op->T.prog4;
   double f64 = 0.0;
   for (double c : P.task_cost) f64 += c;

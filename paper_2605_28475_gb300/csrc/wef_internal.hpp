@@ -21,6 +21,23 @@ struct DevProgram {
 
 constexpr int kCellsPerTile = 32;
 
+// Device copy of the radial-first program (see tables.hpp).
+struct DevRadial {
+  const int4* tasks = nullptr;
+  const int4* chans = nullptr;
+  const int4* m3s = nullptr;
+  const int4* pairs = nullptr;
+  const double2* pw = nullptr;
+  const int32_t* order = nullptr;
+  int ntasks = 0;
+  int n1max = 1;
+};
+
+// Radial-first evaluation: FP32 re-tiling of f, then the persistent radial-first
+// kernel (queue reset here).  ftile32 and queue live in the caller's workspace.
+cudaError_t launch_rf(int K, const double* f, float* ftile32, int* queue, double* q, int64_t ncells, int NQ,
+                      const DevRadial& r, const float* R32, int nsm, cudaStream_t s);
+
 // f[ncells][K][NQ] -> ftile[tile][q][k][32] (zero-padded tail cells).
 cudaError_t launch_tile_f(const double* f, double* ftile, int64_t ncells, int K, int NQ, cudaStream_t s);
 

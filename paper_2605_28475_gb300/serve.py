@@ -1,13 +1,14 @@
 """Continuous-batching request loop for Q(f, f) evaluations (host orchestration only).
 
-Requests (a batch of cells of one (Kmax, Lmax) operator) arrive over time.  Each is
-admitted as soon as a stream slot and enough of a fixed device arena are free: its
-coefficients are copied into the arena (device-resident from then on), its evaluation
-is launched through the C ABI on the slot's stream, and it completes when the
-slot's event fires.  Requests that arrive while others are on the GPU are admitted
-in the same way, so their kernels overlap on the device.  Requests larger than the
-whole arena are rejected.  Nothing here computes: every evaluation is a wef_evaluate
-call.
+Requests (a batch of cells of one (Kmax, Lmax) operator) arrive over time and wait in
+a FIFO.  Whenever one of the stream slots is free, the scheduler takes the shape of
+the oldest waiting request and packs every waiting request of that shape (in arrival
+order, up to a cell cap and what the device arena can hold) into one batch: their
+coefficients are copied into one contiguous arena region (device-resident from then
+on) and evaluated by a single wef_evaluate call on the slot's stream.  Requests that
+arrive while batches are on the GPU join the next batch of their shape, and batches
+on different slots overlap on the device.  Requests larger than the whole arena are
+rejected.  Nothing here computes: every evaluation is a wef_evaluate call.
 """
 import heapq
 import math
@@ -55,6 +56,12 @@ class Arena:
     def ptr(self, o):
         return self.base + o
 
+    def view(self, o, n_doubles):
+        import torch
+
+        return torch.empty(0, dtype=torch.float64, device=self.buf.device).set_(self.buf.untyped_storage(), o // 8,
+                                                                                 (int(n_doubles),))
+
 
 @dataclass(order=True)
 class Request:
@@ -67,10 +74,16 @@ class Request:
     q: object = field(default=None, compare=False, repr=False)
 
 
+def _n_per_cell(shape):
+    km, lm = shape
+    return (km + 1) * (lm + 1) ** 2
+
+
 class Server:
     """ops: {(kmax, lmax): Operator with an uploaded core}."""
 
-    def __init__(self, ops, arena_bytes, nslots=8, precision="tf32", device="cuda:0", keep_results=False):
+    def __init__(self, ops, arena_bytes, nslots=8, precision="tf32", device="cuda:0", max_batch_cells=16384,
+                 keep_results=False):
         import torch
 
         self.torch = torch
@@ -79,76 +92,103 @@ class Server:
         self.dev = torch.device(device)
         self.arena = Arena(arena_bytes, self.dev)
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(nslots)]
-        self.slot_busy = [None] * nslots  # (request, event, allocations)
+        self.slot_busy = [None] * nslots  # (requests, event, allocations, q offset)
+        self.max_batch_cells = int(max_batch_cells)
         self.keep = keep_results
         self.completed = []
         self.rejected = []
+        self.batches = 0
 
-    def _need(self, req):
-        km, lm = req.shape
-        n = req.f.shape[0]
-        N = (km + 1) * (lm + 1) ** 2
-        ws = wef_workspace_size(self.ops[req.shape].h, n, self.prec)
-        return [n * N * 8, n * N * 8, max(ws, 256)]
+    def _bytes(self, shape, ncells):
+        N = _n_per_cell(shape)
+        ws = wef_workspace_size(self.ops[shape].h, ncells, self.prec)
+        return [ncells * N * 8, ncells * N * 8, max(ws, 256)]
 
     def fits_ever(self, req):
-        return sum((b + 255) // 256 * 256 for b in self._need(req)) <= self.arena.size
+        return sum((b + 255) // 256 * 256 for b in self._bytes(req.shape, req.f.shape[0])) <= self.arena.size
 
-    def try_admit(self, req, now):
-        """Admit `req` into a free slot if the arena has room; returns True on success."""
-        torch = self.torch
-        slot = next((i for i, b in enumerate(self.slot_busy) if b is None), None)
-        if slot is None:
-            return False
+    def _alloc(self, sizes):
         allocs = []
-        for nb in self._need(req):
+        for nb in sizes:
             a = self.arena.alloc(nb)
             if a is None:
                 for o, ln in allocs:
                     self.arena.release(o, ln)
-                return False
+                return None
             allocs.append(a)
+        return allocs
+
+    def try_launch(self, waiting, now):
+        """Pack waiting requests of the oldest request's shape into one batch on a free slot.
+        Removes the launched requests from `waiting`; returns True if a batch was launched."""
+        torch = self.torch
+        slot = next((i for i, b in enumerate(self.slot_busy) if b is None), None)
+        if slot is None or not waiting:
+            return False
+        shape = waiting[0].shape
+        chosen, cells = [], 0
+        for r in waiting:
+            if r.shape != shape:
+                continue
+            n = r.f.shape[0]
+            if chosen and cells + n > self.max_batch_cells:
+                break
+            chosen.append(r)
+            cells += n
+        allocs = self._alloc(self._bytes(shape, cells))
+        while allocs is None and len(chosen) > 1:  # shrink the batch to what memory allows
+            cells -= chosen.pop().f.shape[0]
+            allocs = self._alloc(self._bytes(shape, cells))
+        if allocs is None:
+            return False
+        ids = {id(r) for r in chosen}
+        waiting[:] = [r for r in waiting if id(r) not in ids]
         (fo, _), (qo, _), (wo, wn) = allocs
+        N = _n_per_cell(shape)
         st = self.streams[slot]
-        n = req.f.shape[0]
-        fdev = self.arena.ptr(fo)
-        qdev = self.arena.ptr(qo)
-        host = torch.from_numpy(req.f.reshape(-1))
-        # pinned staging keeps the copy asynchronous on the slot's stream
-        pinned = host.pin_memory()
-        dst = torch.empty(0, dtype=torch.float64, device=self.dev).set_(
-            self.arena.buf.untyped_storage(), fo // 8, (pinned.numel(),))
+        staging = []
         with torch.cuda.stream(st):
-            dst.copy_(pinned, non_blocking=True)
-            wef_evaluate(self.ops[req.shape].h, fdev, qdev, n, self.prec, self.arena.ptr(wo), wn, st.cuda_stream)
+            off = 0
+            for r in chosen:
+                n = r.f.shape[0]
+                pinned = torch.from_numpy(r.f.reshape(-1)).pin_memory()
+                self.arena.view(fo + off * N * 8, n * N).copy_(pinned, non_blocking=True)
+                staging.append(pinned)
+                r.admitted = now
+                off += n
+            wef_evaluate(self.ops[shape].h, self.arena.ptr(fo), self.arena.ptr(qo), cells, self.prec,
+                         self.arena.ptr(wo), wn, st.cuda_stream)
             ev = torch.cuda.Event()
             ev.record(st)
-        req.admitted = now
-        self.slot_busy[slot] = (req, ev, allocs, pinned)
+        self.slot_busy[slot] = (chosen, ev, allocs, staging)
+        self.batches += 1
         return True
 
     def poll(self, now_fn):
-        """Complete every request whose event has fired; returns how many completed."""
-        torch = self.torch
+        """Complete every batch whose event has fired; returns how many requests completed."""
         k = 0
         for i, b in enumerate(self.slot_busy):
             if b is None:
                 continue
-            req, ev, allocs, _pinned = b
-            if ev.query():
-                req.done = now_fn()
+            chosen, ev, allocs, _staging = b
+            if not ev.query():
+                continue
+            t = now_fn()
+            qo = allocs[1][0]
+            off = 0
+            for r in chosen:
+                n = r.f.shape[0]
+                N = _n_per_cell(r.shape)
+                r.done = t
                 if self.keep:
-                    km, lm = req.shape
-                    n = req.f.shape[0]
-                    N = (km + 1) * (lm + 1) ** 2
-                    qo = allocs[1][0]
-                    req.q = torch.empty(0, dtype=torch.float64, device=self.dev).set_(
-                        self.arena.buf.untyped_storage(), qo // 8, (n * N,)).clone().reshape(n, km + 1, -1)
-                for o, ln in allocs:
-                    self.arena.release(o, ln)
-                self.slot_busy[i] = None
-                self.completed.append(req)
+                    km, lm = r.shape
+                    r.q = self.arena.view(qo + off * N * 8, n * N).clone().reshape(n, km + 1, -1)
+                off += n
+                self.completed.append(r)
                 k += 1
+            for o, ln in allocs:
+                self.arena.release(o, ln)
+            self.slot_busy[i] = None
         return k
 
     def idle(self):
@@ -176,7 +216,7 @@ def run(server, requests, time_limit=None):
     returns a summary with p50/p99 arrival-to-completion latency and throughput."""
     pending = list(requests)
     heapq.heapify(pending)
-    waiting = []  # arrived, not yet admitted (FIFO)
+    waiting = []  # arrived, not yet launched (FIFO)
     t0 = time.perf_counter()
     now = lambda: time.perf_counter() - t0  # noqa: E731
     last_arrival = requests[-1].arrival if requests else 0.0
@@ -188,15 +228,17 @@ def run(server, requests, time_limit=None):
                 waiting.append(r)
             else:
                 server.rejected.append(r)
-        while waiting and server.try_admit(waiting[0], now()):
-            waiting.pop(0)
         server.poll(now)
+        while server.try_launch(waiting, now()):
+            pass
         if time_limit is not None and t > time_limit + last_arrival:
             break
         if not waiting and pending and server.idle():
             dt = pending[0].arrival - now()
             if dt > 0:
                 time.sleep(min(dt, 0.002))
+        elif not server.idle():
+            time.sleep(0.0002)
     wall = now()
     lat = np.array([r.done - r.arrival for r in server.completed])
     cells = int(sum(r.f.shape[0] for r in server.completed))
@@ -204,6 +246,7 @@ def run(server, requests, time_limit=None):
         "requests": len(requests),
         "completed": len(server.completed),
         "rejected": len(server.rejected),
+        "batches": server.batches,
         "cells": cells,
         "wall_s": wall,
         "cells_per_s": cells / wall if wall > 0 else 0.0,

@@ -177,3 +177,49 @@ def test_mixed_full_size_sampled(prec):
     err = _rel(Q[idx], _oracle(km, lm, R, f[idx]))
     print(f"{prec} full-size normwise err {err:.3e}")
     assert err <= MIXED_TOL[prec]
+
+
+# ------------------------------------------------------------------ radial-first (FP32 radial, FP64 angular)
+RF_TOL = 2e-5  # normwise; FP32 radial contractions (f and the core rounded to FP32)
+
+
+@pytest.mark.parametrize("km,lm,ncells", [(0, 0, 3), (1, 2, 1), (2, 3, 70), (4, 4, 33), (4, 6, 40), (8, 8, 37),
+                                          (16, 2, 45), (12, 12, 3), (16, 16, 2)])
+def test_radial_first_random_core(km, lm, ncells):
+    nt = len(gaunt.channels(lm))
+    R = wi.random_core(nt, km, seed=km * 100 + lm + 2)
+    f = wi.random_cells(km, lm, ncells, seed=lm + 2)
+    op = W.Operator(km, lm, 0.0)
+    op.upload_core(R)
+    Q = _gpu_eval(op, f, "rf32")
+    err = _rel(Q, _oracle(km, lm, R, f))
+    print(f"rf32 K={km} L={lm} n={ncells} normwise err {err:.3e}")
+    assert err <= RF_TOL
+
+
+def test_radial_first_invariants_and_rerun():
+    km, lm = 4, 4
+    R = wi.random_core(len(gaunt.channels(lm)), km, seed=3)
+    op = W.Operator(km, lm, 0.0)
+    op.upload_core(R)
+    f = wi.random_cells(km, lm, 50, seed=4)
+    f[0] = 0.0
+    f[0, 0, 0] = 1.0
+    Q = _gpu_eval(op, f, "rf32")
+    assert np.all(Q[:, 0, 0:4] == 0.0) and np.all(Q[:, 1, 0] == 0.0)
+    assert np.all(Q[0] == 0.0)
+    assert np.array_equal(Q, _gpu_eval(op, f, "rf32"))
+
+
+def test_radial_first_full_size_sampled():
+    km = lm = 12
+    ncells = 16384
+    R = wi.random_core(len(gaunt.channels(lm)), km, seed=7)
+    f = wi.two_maxwellians(km, lm, ncells, seed=3, pool=512)
+    op = W.Operator(km, lm, 1.0)
+    op.upload_core(R)
+    Q = _gpu_eval(op, f, "rf32")
+    idx = np.array([0, 4097, 9999, ncells - 1])
+    err = _rel(Q[idx], _oracle(km, lm, R, f[idx]))
+    print(f"rf32 full-size normwise err {err:.3e}")
+    assert err <= RF_TOL

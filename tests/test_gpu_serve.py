@@ -1,0 +1,55 @@
+"""Continuous batching: every request's result is the same alone and in the mix; memory
+admission defers and rejects as it should."""
+import numpy as np
+import pytest
+
+import wef_inputs as wi
+from oracle import gaunt
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2605_28475_gb300 as W  # noqa: E402
+from paper_2605_28475_gb300 import serve  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not __import__("os").path.exists(W.LIB_PATH):
+        from paper_2605_28475_gb300 import build
+
+        build.build()
+
+
+@pytest.mark.parametrize("prec", ["tf32", "fp64"])
+def test_alone_equals_in_mix(prec):
+    shapes = [(4, 4), (6, 6), (8, 8)]
+    ops = {}
+    for i, (km, lm) in enumerate(shapes):
+        op = W.Operator(km, lm, 1.0)
+        op.upload_core(wi.random_core(len(gaunt.channels(lm)), km, seed=40 + i))
+        ops[(km, lm)] = op
+    reqs = serve.poisson_requests(400.0, 0.15, shapes, 200, seed=9,
+                                  make_cells=lambda sh, n, s: wi.random_cells(sh[0], sh[1], n, seed=s))
+    assert len(reqs) > 20
+    # a small arena forces some requests to wait for memory
+    srv = serve.Server(ops, arena_bytes=16 << 20, nslots=3, precision=prec, keep_results=True, max_batch_cells=500)
+    res = serve.run(srv, reqs)
+    assert res["completed"] == len(reqs) and res["rejected"] == 0
+    assert res["batches"] < len(reqs)  # requests were batched together
+    for r in srv.completed:
+        alone = ops[r.shape].evaluate(torch.from_numpy(r.f).cuda(), precision=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(r.q, alone), r.rid
+
+
+def test_rejects_what_never_fits():
+    op = W.Operator(4, 4, 1.0)
+    op.upload_core(wi.random_core(len(gaunt.channels(4)), 4, seed=1))
+    srv = serve.Server({(4, 4): op}, arena_bytes=1 << 20, nslots=2, precision="fp64")
+    big = serve.Request(0.0, 0, (4, 4), wi.random_cells(4, 4, 2000, seed=2))
+    small = serve.Request(0.0, 1, (4, 4), wi.random_cells(4, 4, 10, seed=3))
+    res = serve.run(srv, [big, small])
+    assert res["rejected"] == 1 and res["completed"] == 1 and srv.completed[0].rid == 1
