@@ -6,11 +6,13 @@ mixture projected onto the basis; core from the library's own quadrature.
 The batch (288 MB of f in, 288 MB of Q out) is larger than the 129 MB L2, so no
 flush is needed between steps.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32|bf16|fp64] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision rf32|tf32|bf16|fp64] [--impl ours|reference]
 
-The headline is the mixed path (FP64 angular coupling, radial stage on the tensor
-cores; TF32 by default); the same run also times the other two precisions with the
-same protocol and reports them under "variants" with the speedup over plain FP64.
+The headline is the mixed-precision radial-first path (radial contraction in FP32 with
+FP32 accumulation, the Gaunt reduction and the conservation projection in FP64).  The
+same run also times the angular-first paths (plain FP64; FP64 angular coupling with the
+radial stage on the tcgen05 tensor cores in BF16 or TF32) with the same protocol and
+reports them under "variants" with the speedup over plain FP64.
 Prints one JSON line (rank 0).  Under torchrun every rank evaluates its own batch
 (weak scaling, no data-path collective); the barrier and the max over ranks of
 the timed region are the only collectives.
@@ -43,7 +45,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="tf32", choices=["fp64", "bf16", "tf32", "rf32"])
+    ap.add_argument("--precision", default="rf32", choices=["fp64", "bf16", "tf32", "rf32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ncells", type=int, default=NCELLS)
     ap.add_argument("--cpu-sample-rows", type=int, default=384)
@@ -288,15 +290,16 @@ def bench_serve(args, W, torch, dev, world):
         op = W.Operator(km, lm, 1.0)
         op.upload_core(op.build_core() if real else wi.random_core(op.n_channels, km, seed=300 + i))
         ops[(km, lm)] = op
-    # capacity: full-batch TF32 throughput per shape, in FP64 flops/s
+    # capacity: full-batch throughput per shape at the serving precision
+    prec = W.PRECISIONS[args.precision]
     st = torch.cuda.current_stream(dev)
     cap = {}
     for sh, op in ops.items():
         n = 2048
         f = torch.from_numpy(wi.random_cells(sh[0], sh[1], n, seed=1)).to(dev)
         q = torch.empty_like(f)
-        ws = op.workspace(n, W.WEF_MIXED_TF32, dev)
-        step = lambda: W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), n, W.WEF_MIXED_TF32, ws.data_ptr(), ws.numel(), st.cuda_stream)  # noqa: E731,B023
+        ws = op.workspace(n, prec, dev)
+        step = lambda: W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), n, prec, ws.data_ptr(), ws.numel(), st.cuda_stream)  # noqa: E731,B023
         ms = _time_steps(step, 3, 1, st, torch)
         cap[sh] = n / (ms / 1e3)  # cells/s at this shape
     max_cells = 4096
@@ -307,9 +310,10 @@ def bench_serve(args, W, torch, dev, world):
     rate = 0.7 / mean_service
     reqs = serve.poisson_requests(rate, args.duration, shapes, max_cells, seed=5,
                                   make_cells=lambda sh, n, s: wi.random_cells(sh[0], sh[1], n, seed=s))
-    srv = serve.Server(ops, arena_bytes=24 << 30, nslots=8, precision="tf32", device=str(dev))
+    srv = serve.Server(ops, arena_bytes=24 << 30, nslots=8, precision=args.precision, device=str(dev))
     res = serve.run(srv, reqs)
-    return _line("serve: p50/p99 latency and cells/s", res["cells_per_s"], "cells/s", None, args, world, "f64+tf32",
+    dtype = "f64" if args.precision == "fp64" else f"f64+{args.precision}"
+    return _line("serve: p50/p99 latency and cells/s", res["cells_per_s"], "cells/s", None, args, world, dtype,
                  f"Poisson arrivals at 0.7x capacity ({rate:.1f} req/s) for {args.duration:.0f} s; sizes log-uniform "
                  f"1-{max_cells} cells; Kmax=Lmax in {{8,10,12,16}}; 8 stream slots; 24 GiB admission arena",
                  serving=res, capacity_cells_per_s={f"{k[0]}x{k[1]}": v for k, v in cap.items()})
@@ -388,15 +392,15 @@ def main():
         ms_total = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         ms_step = ms_total / args.steps
         kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
-        fp64_flops, tc_flops = W.wef_flops(op.h, prec)
+        fp64_flops, radial_flops = W.wef_flops(op.h, prec)
         out = {
             "value": job_throughput(world, ncells, ms_step),
             "ms_per_step": ms_step,
             "kernel_ms": kernel_ms,
             "fp64_tflops": fp64_flops * ncells / (kernel_ms / 1e3) / 1e12,
             "fp64_flops_per_cell": fp64_flops,
-            "tc_flops_per_cell": tc_flops,
-            "tc_tflops": tc_flops * ncells / (kernel_ms / 1e3) / 1e12,
+            "radial_flops_per_cell": radial_flops,
+            "radial_tflops": radial_flops * ncells / (kernel_ms / 1e3) / 1e12,
             "step": step,
             "clocks": clk.summary() if clk else None,
         }
@@ -451,16 +455,20 @@ def main():
         },
         "roofline": {
             "bound": "alu",
-            "pipe": "FP64 FMA (angular coupling" + (" + radial contraction)" if args.precision == "fp64" else ")"),
-            "kernel": "fp64_kernel" if args.precision == "fp64" else f"tc_kernel<{KMAX + 1},{args.precision}>",
+            "pipe": {"fp64": "FP64 FMA (angular coupling + radial contraction)",
+                     "rf32": "FP64 FMA (Gaunt reduction of the radial-first products)"}.get(
+                         args.precision, "FP64 FMA (angular coupling)"),
+            "kernel": {"fp64": "fp64_kernel", "rf32": f"rf_kernel<{KMAX + 1}>"}.get(
+                args.precision, f"tc_kernel<{KMAX + 1},{args.precision}>"),
             "achieved": achieved,
             "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": None,
             "fp64_flops_per_cell": head["fp64_flops_per_cell"],
-            "tc_flops_per_cell": head["tc_flops_per_cell"],
-            "tc_tflops": head["tc_tflops"],
+            "radial_flops_per_cell": head["radial_flops_per_cell"],
+            "radial_note": "low-precision radial flops: tensor-core (bf16, tf32) or FP32 CUDA-core (rf32)",
+            "radial_tflops": head["radial_tflops"],
             "kernel_ms": head["kernel_ms"],
             "peak_note": "peak = 152 SMs x 2 DFMA lanes/clock x 2 flop x 2070 MHz; probe = live DFMA chain",
             "peak_probe": probe,

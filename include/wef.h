@@ -149,6 +149,26 @@ wef_status wef_plan_status(wef_plan plan, int reset);
 wef_status wef_plan_destroy(wef_plan plan);
 
 /*
+ * Time integration and linearization (device).
+ *
+ * wef_integrate advances the spatially homogeneous equation df/dt = Q(f, f)
+ * (Sec. 2.1) in place by nsteps classical fourth-order Runge-Kutta steps of size
+ * dt (the explicit time stepping of Sec. 5.3.2), every cell independently, with Q
+ * evaluated at precision `prec`.  Because the projection zeroes the mass, momentum
+ * and energy components of every Q exactly, those components of f do not change.
+ * wef_linearized_apply computes out = L d, L = dQ/dc at the base states c0
+ * (Sec. 5.3.1), as Q(c0 + d) - Q(c0) - Q(d) (exact for the bilinear form; relative
+ * rounding grows like |c0| / |d|).  Both are asynchronous on `stream`, allocate
+ * nothing, and need a workspace of wef_integrate_workspace_size bytes (256-byte
+ * aligned).  c0, d, out: [ncells][K][NQ]; out may not alias the inputs.
+ */
+wef_status wef_integrate_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int64_t* bytes);
+wef_status wef_integrate(wef_op op, double* f_dev, int64_t ncells, double dt, int nsteps, wef_precision prec,
+                         void* workspace, int64_t ws_bytes, void* stream);
+wef_status wef_linearized_apply(wef_op op, const double* c0_dev, const double* d_dev, double* out_dev, int64_t ncells,
+                                wef_precision prec, void* workspace, int64_t ws_bytes, void* stream);
+
+/*
  * wef_core_build - the kinematic core R[c][k1][k2][k3] of the operator by the
  * singular quadrature of Sec. 4.3 / Appendix A-B, on the host (all cores of the
  * machine).  pad_rad / pad_ang are the selective paddings of Appendix B (the

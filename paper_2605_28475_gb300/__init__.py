@@ -56,6 +56,9 @@ def lib():
             "wef_plan_status": ([vp, ctypes.c_int], ctypes.c_int),
             "wef_plan_destroy": ([vp], ctypes.c_int),
             "wef_evaluate_noalloc": ([vp, vp, vp, i64, vp], ctypes.c_int),
+            "wef_integrate_workspace_size": ([vp, i64, ctypes.c_int, i64p], ctypes.c_int),
+            "wef_integrate": ([vp, vp, i64, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, i64, vp], ctypes.c_int),
+            "wef_linearized_apply": ([vp, vp, vp, vp, i64, ctypes.c_int, vp, i64, vp], ctypes.c_int),
             "wef_last_error": ([], ctypes.c_char_p),
             "wef_destroy": ([vp], ctypes.c_int),
         }
@@ -174,6 +177,20 @@ def wef_plan_destroy(plan):
     _check(lib().wef_plan_destroy(plan))
 
 
+def wef_integrate_workspace_size(op, ncells, prec=WEF_FP64):
+    b = ctypes.c_int64()
+    _check(lib().wef_integrate_workspace_size(op, int(ncells), int(prec), ctypes.byref(b)))
+    return b.value
+
+
+def wef_integrate(op, f_ptr, ncells, dt, nsteps, prec, ws_ptr, ws_bytes, stream_ptr):
+    _check(lib().wef_integrate(op, f_ptr, int(ncells), float(dt), int(nsteps), int(prec), ws_ptr, int(ws_bytes), stream_ptr))
+
+
+def wef_linearized_apply(op, c0_ptr, d_ptr, out_ptr, ncells, prec, ws_ptr, ws_bytes, stream_ptr):
+    _check(lib().wef_linearized_apply(op, c0_ptr, d_ptr, out_ptr, int(ncells), int(prec), ws_ptr, int(ws_bytes), stream_ptr))
+
+
 def wef_last_error():
     return lib().wef_last_error().decode()
 
@@ -218,6 +235,42 @@ class Operator:
         st = stream if stream is not None else torch.cuda.current_stream(f.device)
         wef_evaluate(self.h, f.data_ptr(), q.data_ptr(), ncells, prec, ws.data_ptr(), ws.numel(), st.cuda_stream)
         return q
+
+    def _dyn_workspace(self, ncells, prec, device):
+        import torch
+
+        need = wef_integrate_workspace_size(self.h, ncells, prec)
+        ws = getattr(self, "_dws", None)
+        if ws is None or ws.numel() < max(need, 256) or ws.device != device:
+            self._dws = torch.empty(max(need, 256), dtype=torch.uint8, device=device)
+        return self._dws
+
+    def integrate(self, f, dt, nsteps, precision="fp64", stream=None):
+        """Advance df/dt = Q(f, f) in place by `nsteps` RK4 steps of size `dt`."""
+        import torch
+
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        assert f.is_cuda and f.dtype == torch.float64 and f.is_contiguous()
+        ws = self._dyn_workspace(f.shape[0], prec, f.device)
+        st = stream if stream is not None else torch.cuda.current_stream(f.device)
+        wef_integrate(self.h, f.data_ptr(), f.shape[0], dt, nsteps, prec, ws.data_ptr(), ws.numel(), st.cuda_stream)
+        return f
+
+    def linearized_apply(self, c0, d, out=None, precision="fp64", stream=None):
+        """out = L d, L the linearization of Q at the base states c0 (one per cell)."""
+        import torch
+
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        for t in (c0, d):
+            assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+        assert c0.shape == d.shape
+        if out is None:
+            out = torch.empty_like(d)
+        ws = self._dyn_workspace(d.shape[0], prec, d.device)
+        st = stream if stream is not None else torch.cuda.current_stream(d.device)
+        wef_linearized_apply(self.h, c0.data_ptr(), d.data_ptr(), out.data_ptr(), d.shape[0], prec, ws.data_ptr(),
+                             ws.numel(), st.cuda_stream)
+        return out
 
     def close(self):
         if self.h is not None:

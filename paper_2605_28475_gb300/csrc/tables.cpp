@@ -265,8 +265,8 @@ std::string build_tables(int kmax, int lmax, Tables& t) {
     for (size_t i = 0; i < v.size(); ++i)
       if (i == 0 || v[i].q2 != v[i - 1].q2) ++t.n_sym_groups;
   }
-  // Radial-first program: per shell, per channel, group the channel's entries by q3,
-  // then by q2; each (q2, q3) pair feeds at most two q1 of the shell.
+  // Radial-first program: per shell, per channel, group the channel's entries by q2,
+  // then by q3; each (q2, q3) pair feeds at most two q1 of the shell.
   {
     RadialProgram& RP = t.rprog;
     RP = RadialProgram();
@@ -279,27 +279,27 @@ std::string build_tables(int kmax, int lmax, Tables& t) {
       double cost = 0.0;
       for (int sc = 0; sc < NS; ++sc) {
         if (t.chans[t.sym_chan[sc]].l1 != l1) continue;
-        // (q3, q2) -> list of (q1 offset, w)
+        // (q2, q3) -> list of (q1 offset, w)
         std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> byp;
         for (int m = 0; m < n1; ++m)
-          for (const Entry& e : sl[(size_t)sc * t.NQ + q1b + m]) byp[{e.q3, e.q2}].push_back({m, e.w});
+          for (const Entry& e : sl[(size_t)sc * t.NQ + q1b + m]) byp[{e.q2, e.q3}].push_back({m, e.w});
         if (byp.empty()) continue;
-        const int ms = (int)RP.m3s.size() / 4;
-        int nm3 = 0, cur_q3 = -1;
+        const int ms = (int)RP.outer.size() / 4;
+        int nm3 = 0, cur_q2 = -1;
         for (const auto& kv : byp) {
-          const int q3 = kv.first.first, q2 = kv.first.second;
-          if (q3 != cur_q3) {
-            RP.m3s.insert(RP.m3s.end(), {q3, (int32_t)(RP.pairs.size() / 4), 0, 0});
-            cur_q3 = q3;
+          const int q2 = kv.first.first, q3 = kv.first.second;
+          if (q2 != cur_q2) {
+            RP.outer.insert(RP.outer.end(), {q2, (int32_t)(RP.pairs.size() / 4), 0, 0});
+            cur_q2 = q2;
             ++nm3;
             cost += 2.0 * K * K * K;
           }
           const auto& v = kv.second;
           if (v.size() > 2) return "a radial-first pair feeding more than two q1";
-          RP.pairs.insert(RP.pairs.end(), {q2, (int32_t)v.size(), v[0].first, v.size() > 1 ? v[1].first : v[0].first});
+          RP.pairs.insert(RP.pairs.end(), {q3, (int32_t)v.size(), v[0].first, v.size() > 1 ? v[1].first : v[0].first});
           RP.pw.push_back(v[0].second);
           RP.pw.push_back(v.size() > 1 ? v[1].second : 0.0);
-          RP.m3s[RP.m3s.size() - 2] += 1;
+          RP.outer[RP.outer.size() - 2] += 1;
           cost += 2.0 * K * K + 2.0 * K * (double)v.size();
           RP.fp32_flops += 2.0 * K * K;
           RP.fp64_flops += 2.0 * K * (double)v.size();

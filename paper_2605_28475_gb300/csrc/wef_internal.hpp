@@ -25,7 +25,7 @@ constexpr int kCellsPerTile = 32;
 struct DevRadial {
   const int4* tasks = nullptr;
   const int4* chans = nullptr;
-  const int4* m3s = nullptr;
+  const int4* outer = nullptr;
   const int4* pairs = nullptr;
   const double2* pw = nullptr;
   const int32_t* order = nullptr;
@@ -33,10 +33,16 @@ struct DevRadial {
   int n1max = 1;
 };
 
+// Radial-first core layout: k1 padded to an even count, k2 to whole float4s.
+inline int rf_k1_padded(int K) { return (K + 1) / 2 * 2; }
+inline int rf_k2_padded(int K) { return (K + 3) / 4 * 4; }
+
 // Radial-first evaluation: FP32 re-tiling of f, then the persistent radial-first
 // kernel (queue reset here).  ftile32 and queue live in the caller's workspace.
+// ev0/ev1 (may be null) are recorded around the contraction kernel alone.
 cudaError_t launch_rf(int K, const double* f, float* ftile32, int* queue, double* q, int64_t ncells, int NQ,
-                      const DevRadial& r, const float* R32, int nsm, cudaStream_t s);
+                      const DevRadial& r, const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                      cudaEvent_t ev1 = nullptr);
 
 // f[ncells][K][NQ] -> ftile[tile][q][k][32] (zero-padded tail cells).
 cudaError_t launch_tile_f(const double* f, double* ftile, int64_t ncells, int K, int NQ, cudaStream_t s);

@@ -23,7 +23,7 @@ def need_gpu():
         build.build()
 
 
-@pytest.mark.parametrize("prec", ["tf32", "fp64"])
+@pytest.mark.parametrize("prec", ["tf32", "fp64", "rf32"])
 def test_alone_equals_in_mix(prec):
     shapes = [(4, 4), (6, 6), (8, 8)]
     ops = {}
