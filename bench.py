@@ -50,10 +50,11 @@ def parse():
     ap.add_argument("--ncells", type=int, default=NCELLS)
     ap.add_argument("--cpu-sample-rows", type=int, default=384)
     ap.add_argument("--cpu-sample-cells", type=int, default=4)
-    ap.add_argument("--workload", default="kl12", choices=["kl12", "maxwell4", "hs8", "ragged", "serve"],
+    ap.add_argument("--workload", default="kl12", choices=["kl12", "maxwell4", "hs8", "ragged", "serve", "baselines"],
                     help="kl12: hard spheres K=L=12 x 16384 cells (default); maxwell4: one Maxwell cell at "
                          "K=L=4; hs8: hard spheres K=L=8 x 4096 cells; ragged: VHS, 32768 cells with "
-                         "(Kmax, Lmax) drawn from {6,8,10,12,16}; serve: Poisson request stream")
+                         "(Kmax, Lmax) drawn from {6,8,10,12,16}; serve: Poisson request stream; baselines: "
+                         "factorised vs naive-COO vs dense tensor at K=L=8")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     return ap.parse_args()
 
@@ -237,6 +238,47 @@ def bench_small(args, W, torch, dev, world, kind):
                            "note": "whole step (re-tiling + contraction)"})
 
 
+def bench_baselines(args, W, torch, dev, world):
+    """Factorised vs unfactorised on the same GPU (Sec. 4.5), hard spheres, Kmax=Lmax=8,
+    two-Maxwellian cells, core from the library quadrature: plain FP64 (angular-first),
+    radial-first (FP32 radial, FP64 reduction), naive COO loop (FP64) and dense tensor
+    (cuBLAS FP64 GEMMs over the assembled N^3 tensor)."""
+    import wef_inputs as wi
+
+    km = 8
+    op = W.Operator(km, km, 1.0)
+    op.upload_core(op.build_core())
+    st = torch.cuda.current_stream(dev)
+    n_fact, n_dense = 4096, 256
+    f_host = wi.two_maxwellians(km, km, n_fact, seed=2, pool=1024)
+    f = torch.from_numpy(f_host).to(dev)
+    q = torch.empty_like(f)
+    res = {}
+    for name, prec in (("fp64", 0), ("rf32", W.PRECISIONS["rf32"])):
+        ws = op.workspace(n_fact, prec, dev)
+        step = lambda: W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), n_fact, prec, ws.data_ptr(), ws.numel(), st.cuda_stream)  # noqa: E731,B023
+        res[name] = n_fact / (_time_steps(step, max(args.steps, 5), args.warmup, st, torch) / 1e3)
+    ws = torch.empty(max(W.wef_workspace_size(op.h, n_fact, 0), 256), dtype=torch.uint8, device=dev)
+    step = lambda: W.wef_naive_evaluate(op.h, f.data_ptr(), q.data_ptr(), n_fact, ws.data_ptr(), ws.numel(), st.cuda_stream)  # noqa: E731
+    res["naive_coo"] = n_fact / (_time_steps(step, max(args.steps, 3), args.warmup, st, torch) / 1e3)
+    C = torch.empty(W.wef_dense_tensor_size(op.h) // 8, dtype=torch.float64, device=dev)
+    W.wef_dense_assemble(op.h, C.data_ptr(), C.numel() * 8, st.cuda_stream)
+    wsd = torch.empty(W.wef_dense_workspace_size(op.h, n_dense), dtype=torch.uint8, device=dev)
+    fd = f[:n_dense].contiguous()
+    qd = torch.empty_like(fd)
+    step = lambda: W.wef_dense_evaluate(op.h, C.data_ptr(), fd.data_ptr(), qd.data_ptr(), n_dense, wsd.data_ptr(), wsd.numel(), st.cuda_stream)  # noqa: E731
+    res["dense"] = n_dense / (_time_steps(step, 3, 2, st, torch) / 1e3)
+    N, K, rfp = op.N, km + 1, W.PRECISIONS["rf32"]
+    n_sym = W.wef_flops(op.h, rfp)[0] / (2 * K)  # symmetrised Gaunt entries (2K FP64 flops each there)
+    return _line("Q(f,f) cell-evals/s at K=L=8, factorised vs unfactorised (FP64)", res["fp64"], "cells/s", None, args,
+                 world, "f64", f"hard spheres, Kmax=Lmax=8, two-Maxwellian cells ({n_fact} per batch; dense: {n_dense}), "
+                 f"core from the library quadrature",
+                 cells_per_s=res, speedup_vs_dense={k: v / res["dense"] for k, v in res.items()},
+                 flops_per_cell={"dense": 2.0 * N**3, "naive_coo": n_sym * 2.0 * (K**3 + K**2 + K),
+                                 "fp64": W.wef_flops(op.h, 0)[0], "rf32_fp64": W.wef_flops(op.h, rfp)[0],
+                                 "rf32_fp32": W.wef_flops(op.h, rfp)[1]})
+
+
 def bench_ragged(args, W, torch, dev, world, ncells=32768, seed=4):
     """VHS gamma=0.5, ncells cells with (Kmax, Lmax) drawn independently from {6,8,10,12,16},
     grouped by shape; one persistent TF32 launch replayed from a CUDA graph, autotuned."""
@@ -340,7 +382,8 @@ def main():
         fn = {"maxwell4": lambda: bench_small(args, W, torch, dev, world, "maxwell4"),
               "hs8": lambda: bench_small(args, W, torch, dev, world, "hs8"),
               "ragged": lambda: bench_ragged(args, W, torch, dev, world),
-              "serve": lambda: bench_serve(args, W, torch, dev, world)}[args.workload]
+              "serve": lambda: bench_serve(args, W, torch, dev, world),
+              "baselines": lambda: bench_baselines(args, W, torch, dev, world)}[args.workload]
         line = fn()
         if rank == 0:
             print(json.dumps(line), flush=True)

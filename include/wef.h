@@ -149,6 +149,29 @@ wef_status wef_plan_status(wef_plan plan, int reset);
 wef_status wef_plan_destroy(wef_plan plan);
 
 /*
+ * Unfactorised baselines (Sec. 4.5): the same Q(f, f), FP64, without the factorisation,
+ * for comparison on the same GPU.  Both use the uploaded (symmetrised, zeroed) core.
+ *
+ * wef_naive_evaluate: the COO loop of Sec. 4.5.2 - for every non-zero Gaunt entry the
+ *   full K^3 radial sum.  f_dev, q_dev: [ncells][K][NQ]; workspace: at least
+ *   wef_workspace_size(op, ncells, WEF_FP64) bytes, 256-byte aligned.  Asynchronous.
+ * wef_dense_tensor_size / wef_dense_assemble: the dense tensor C[a1][a2][a3] of Sec. 4.5.1
+ *   (N^3 doubles, N = K NQ; 85 GB at Kmax = Lmax = 12) written by the library into a
+ *   caller-owned device buffer; rows of the collision invariants are zero.
+ * wef_dense_evaluate: Q_a1 = sum_{a2,a3} C[a1][a2][a3] f_a2 f_a3 as two cuBLAS FP64 GEMMs
+ *   per chunk of cells (chunk = ws_bytes / (N^2 * 8); wef_dense_workspace_size suggests
+ *   a workspace for up to 256 cells per chunk).  Asynchronous on `stream`.
+ * Errors: WEF_EINVAL (NULL buffer, short buffer or workspace), WEF_ENOCORE, WEF_ECUDA.
+ */
+wef_status wef_naive_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t ncells, void* workspace,
+                              int64_t ws_bytes, void* stream);
+wef_status wef_dense_tensor_size(wef_op op, int64_t* bytes);
+wef_status wef_dense_assemble(wef_op op, double* C_dev, int64_t bytes, void* stream);
+wef_status wef_dense_workspace_size(wef_op op, int64_t ncells, int64_t* bytes);
+wef_status wef_dense_evaluate(wef_op op, const double* C_dev, const double* f_dev, double* q_dev, int64_t ncells,
+                              void* workspace, int64_t ws_bytes, void* stream);
+
+/*
  * Time integration and linearization (device).
  *
  * wef_integrate advances the spatially homogeneous equation df/dt = Q(f, f)
@@ -176,6 +199,17 @@ wef_status wef_linearized_apply(wef_op op, const double* c0_dev, const double* d
  * conservation zeroing is applied (pass WEF_CORE_APPLY_NULLSPACE to upload).
  */
 wef_status wef_core_build(wef_op op, int pad_rad, int pad_ang, double* R_out, int64_t len);
+
+/*
+ * wef_core_build_device - the same core by the same quadrature (Sec. 4.3, Appendix A-B:
+ * rules, point counts, paddings, Funk-Hecke sphere means) assembled on the current GPU
+ * in FP64: point tables per chunk of z nodes, then one CTA per channel accumulating the
+ * rank-1 radial terms.  Synchronous; allocates its device scratch (about 1 GB at most
+ * for the point tables plus the core) and frees it before returning.  R_out: host array
+ * of length N_T*K^3, the raw core as wef_core_build returns it (agrees with it to
+ * rounding).  Errors: WEF_EINVAL, WEF_ESHAPE (len), WEF_ECUDA.
+ */
+wef_status wef_core_build_device(wef_op op, int pad_rad, int pad_ang, double* R_out, int64_t len);
 
 /*
  * wef_flops - arithmetic the evaluation executes per cell: FP64 flops (angular

@@ -45,6 +45,7 @@ def lib():
             "wef_workspace_size": ([vp, i64, ctypes.c_int, i64p], ctypes.c_int),
             "wef_evaluate": ([vp, vp, vp, i64, ctypes.c_int, vp, i64, vp], ctypes.c_int),
             "wef_core_build": ([vp, ctypes.c_int, ctypes.c_int, dp, i64], ctypes.c_int),
+            "wef_core_build_device": ([vp, ctypes.c_int, ctypes.c_int, dp, i64], ctypes.c_int),
             "wef_flops": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
             "wef_set_trace_events": ([vp, vp, vp], ctypes.c_int),
             "wef_device_status": ([vp, ctypes.c_int], ctypes.c_int),
@@ -59,6 +60,11 @@ def lib():
             "wef_integrate_workspace_size": ([vp, i64, ctypes.c_int, i64p], ctypes.c_int),
             "wef_integrate": ([vp, vp, i64, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, i64, vp], ctypes.c_int),
             "wef_linearized_apply": ([vp, vp, vp, vp, i64, ctypes.c_int, vp, i64, vp], ctypes.c_int),
+            "wef_naive_evaluate": ([vp, vp, vp, i64, vp, i64, vp], ctypes.c_int),
+            "wef_dense_tensor_size": ([vp, i64p], ctypes.c_int),
+            "wef_dense_assemble": ([vp, vp, i64, vp], ctypes.c_int),
+            "wef_dense_workspace_size": ([vp, i64, i64p], ctypes.c_int),
+            "wef_dense_evaluate": ([vp, vp, vp, vp, i64, vp, i64, vp], ctypes.c_int),
             "wef_last_error": ([], ctypes.c_char_p),
             "wef_destroy": ([vp], ctypes.c_int),
         }
@@ -123,6 +129,13 @@ def wef_core_build(op, pad_rad=20, pad_ang=20):
     n = wef_sizes(op)[3]
     R = np.empty(n, np.float64)
     _check(lib().wef_core_build(op, int(pad_rad), int(pad_ang), _dp(R), n))
+    return R
+
+
+def wef_core_build_device(op, pad_rad=20, pad_ang=20):
+    n = wef_sizes(op)[3]
+    R = np.empty(n, np.float64)
+    _check(lib().wef_core_build_device(op, int(pad_rad), int(pad_ang), _dp(R), n))
     return R
 
 
@@ -191,6 +204,30 @@ def wef_linearized_apply(op, c0_ptr, d_ptr, out_ptr, ncells, prec, ws_ptr, ws_by
     _check(lib().wef_linearized_apply(op, c0_ptr, d_ptr, out_ptr, int(ncells), int(prec), ws_ptr, int(ws_bytes), stream_ptr))
 
 
+def wef_naive_evaluate(op, f_ptr, q_ptr, ncells, ws_ptr, ws_bytes, stream_ptr):
+    _check(lib().wef_naive_evaluate(op, f_ptr, q_ptr, int(ncells), ws_ptr, int(ws_bytes), stream_ptr))
+
+
+def wef_dense_tensor_size(op):
+    b = ctypes.c_int64()
+    _check(lib().wef_dense_tensor_size(op, ctypes.byref(b)))
+    return b.value
+
+
+def wef_dense_assemble(op, c_ptr, nbytes, stream_ptr):
+    _check(lib().wef_dense_assemble(op, c_ptr, int(nbytes), stream_ptr))
+
+
+def wef_dense_workspace_size(op, ncells):
+    b = ctypes.c_int64()
+    _check(lib().wef_dense_workspace_size(op, int(ncells), ctypes.byref(b)))
+    return b.value
+
+
+def wef_dense_evaluate(op, c_ptr, f_ptr, q_ptr, ncells, ws_ptr, ws_bytes, stream_ptr):
+    _check(lib().wef_dense_evaluate(op, c_ptr, f_ptr, q_ptr, int(ncells), ws_ptr, int(ws_bytes), stream_ptr))
+
+
 def wef_last_error():
     return lib().wef_last_error().decode()
 
@@ -209,8 +246,10 @@ class Operator:
         self.N, self.n_channels, self.n_gaunt, self.core_len = wef_sizes(self.h)
         self._ws = None
 
-    def build_core(self, pad_rad=20, pad_ang=20):
-        return wef_core_build(self.h, pad_rad, pad_ang).reshape(self.n_channels, self.K, self.K, self.K)
+    def build_core(self, pad_rad=20, pad_ang=20, device=False):
+        """The raw kinematic core [channel][k1][k2][k3]: host builder, or the GPU one (device=True)."""
+        fn = wef_core_build_device if device else wef_core_build
+        return fn(self.h, pad_rad, pad_ang).reshape(self.n_channels, self.K, self.K, self.K)
 
     def upload_core(self, R, flags=WEF_CORE_APPLY_NULLSPACE):
         wef_upload_core(self.h, R, flags)

@@ -60,7 +60,7 @@ def build(verbose=False, extra_nvcc=()):
     with cf.ThreadPoolExecutor(max_workers=2) as ex:
         fut = ex.submit(_compile, jobs_probe)
         tmp = LIB + ".tmp"
-        _compile([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"])
+        _compile([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas", "-lpthread"])
         os.replace(tmp, LIB)
         fut.result()
     return LIB

@@ -19,6 +19,7 @@
 #include <thread>
 #include <vector>
 
+#include "core_quad.hpp"
 #include "tables.hpp"
 
 namespace wef {
@@ -156,17 +157,7 @@ Rule gl01(int n) {
   return r;
 }
 
-struct Ctx {
-  int kmax, lmax, K, L1, NT;
-  double gamma;
-  std::vector<double> Nkl;      // [k][l]
-  std::vector<double> ylm_norm; // [l][m], m >= 0, cos-type normalisation incl. sqrt2
-  std::vector<Channel> ch;
-  std::vector<double> Ghat;     // [c][m] = G[(l1 m),(l2 0),(l3 m)], m = 0..min(l1,l3)
-  std::vector<int> Ghat_off;
-  std::vector<double> s2;       // [c] Y_{l2 0}(z_hat)
-  Rule ft;                      // Funk-Hecke rule on [-1, 1]
-};
+using Ctx = CoreQuad;
 
 // cos-type real harmonics at a direction with polar cosine ct and azimuth 0:
 // out[l*(L+1)+m], m = 0..l.
@@ -213,16 +204,16 @@ void radial_all(const Ctx& C, double v, double* out) {
 
 // eps_{kl}(Vm, rho) for all (k, l): out[k*(L+1)+l].
 void sphere_mean(const Ctx& C, double Vm, double rho, double* out, double* scratch) {
-  const int n = (int)C.ft.x.size();
+  const int n = (int)C.ftx.size();
   std::fill(out, out + C.K * C.L1, 0.0);
   for (int i = 0; i < n; ++i) {
-    const double t = C.ft.x[i];
+    const double t = C.ftx[i];
     const double r2 = Vm * Vm + rho * rho + 2.0 * Vm * rho * t;
     const double r = std::sqrt(std::max(r2, 0.0));
     const double ca = r > 0 ? (Vm + rho * t) / r : 1.0;
     radial_all(C, r, scratch);
     double p0 = 1.0, p1 = ca;
-    const double wt = 0.5 * C.ft.w[i];
+    const double wt = 0.5 * C.ftw[i];
     for (int l = 0; l < C.L1; ++l) {
       double pl;
       if (l == 0) pl = 1.0;
@@ -267,9 +258,8 @@ void channel_terms(const Ctx& C, double v, double w, double cb, double y, double
 
 }  // namespace
 
-// Returns "" on success.
-std::string core_build(const Tables& T, double gamma, int pad_rad, int pad_ang, double* R) {
-  Ctx C;
+std::string core_quadrature(const Tables& T, double gamma, int pad_rad, int pad_ang, CoreQuad& C) {
+  C = CoreQuad();
   C.kmax = T.kmax;
   C.lmax = T.lmax;
   C.K = T.K;
@@ -294,13 +284,9 @@ std::string core_build(const Tables& T, double gamma, int pad_rad, int pad_ang, 
     for (int m = 0; m <= std::min(h.l1, h.l3); ++m) C.Ghat.push_back(real_gaunt(h.l1, m, h.l2, 0, h.l3, m));
   }
   // channel norms S_c = sum_m g^2 over all m-triples
-  std::vector<double> S(C.NT, 0.0);
-  for (size_t z = 0; z < T.g.size(); ++z) S[T.c[z]] += T.g[z] * T.g[z];
-  {
-    Rule r;
-    gauss_legendre((C.kmax + C.lmax) / 2 + 2, r.x, r.w);
-    C.ft = r;
-  }
+  C.S.assign(C.NT, 0.0);
+  for (size_t z = 0; z < T.g.size(); ++z) C.S[T.c[z]] += T.g[z] * T.g[z];
+  gauss_legendre((C.kmax + C.lmax) / 2 + 2, C.ftx, C.ftw);
   // Table 2 / Appendix B point counts plus padding.
   const int kmax = C.kmax, lmax = C.lmax;
   const int Nz = (int)std::ceil((3.0 * kmax + 1.5 * lmax + 3.0) / 2.0) + pad_rad;
@@ -308,9 +294,29 @@ std::string core_build(const Tables& T, double gamma, int pad_rad, int pad_ang, 
   const int Nh1 = kmax + (int)std::ceil(1.5 * lmax) + 1 + pad_ang;
   const int Ny2 = 4 * kmax + 3 * lmax + 4 + pad_ang;
   const int Nh2 = 3 * kmax + (int)std::floor(1.5 * lmax) + 3 + pad_rad;
-  std::vector<double> zz, wz;
-  gauss_laguerre(Nz, 0.5 * gamma, zz, wz);
-  const Rule rx1 = gl01(Nx1), rh1 = gl01(Nh1), ry2 = gl01(Ny2), rh2 = gl01(Nh2);
+  gauss_laguerre(Nz, 0.5 * gamma, C.zz, C.wz);
+  Rule r;
+  r = gl01(Nx1); C.x1 = r.x; C.wx1 = r.w;
+  r = gl01(Nh1); C.h1 = r.x; C.wh1 = r.w;
+  r = gl01(Ny2); C.y2 = r.x; C.wy2 = r.w;
+  r = gl01(Nh2); C.h2 = r.x; C.wh2 = r.w;
+  C.pref = std::pow(2.0, gamma) * 4.0 / std::pow(2.0 * M_PI, 3.0);
+  return "";
+}
+
+// Returns "" on success.
+std::string core_build(const Tables& T, double gamma, int pad_rad, int pad_ang, double* R) {
+  CoreQuad C;
+  std::string err = core_quadrature(T, gamma, pad_rad, pad_ang, C);
+  if (!err.empty()) return err;
+  const std::vector<double>& S = C.S;
+  const std::vector<double>&zz = C.zz, &wz = C.wz;
+  const int Nz = (int)zz.size(), Nx1 = (int)C.x1.size(), Nh1 = (int)C.h1.size(), Ny2 = (int)C.y2.size(),
+            Nh2 = (int)C.h2.size();
+  struct R01 {
+    const std::vector<double>&x, &w;
+  };
+  const R01 rx1{C.x1, C.wx1}, rh1{C.h1, C.wh1}, ry2{C.y2, C.wy2}, rh2{C.h2, C.wh2};
   const int K = C.K, L1 = C.L1, NT = C.NT;
   const size_t RL = (size_t)NT * K * K * K;
   // work items: (z, outer node, patch, half)
@@ -326,7 +332,7 @@ std::string core_build(const Tables& T, double gamma, int pad_rad, int pad_ang, 
   unsigned nth = std::max(1u, std::thread::hardware_concurrency());
   std::vector<std::vector<double>> acc(nth);
   std::atomic<size_t> next(0);
-  const double pref = std::pow(2.0, gamma) * 4.0 / std::pow(2.0 * M_PI, 3.0);
+  const double pref = C.pref;
   auto worker = [&](unsigned tid) {
     std::vector<double>& Racc = acc[tid];
     Racc.assign(RL, 0.0);

@@ -7,10 +7,11 @@
 // cell at K=L=12 instead of 19.5 MFLOP for the angular-first coupling) and moves the
 // dense K^3 / K^2 work to the FP32 pipe, which is ~60x faster.
 //
-// CTA = 32 cells x ceil(K/2) warps (lane = cell, two k1 per warp).  A persistent grid
-// pulls (shell, tile) items from a queue, largest shells first; each item accumulates
-// the shell's Q[k1, q1] in shared memory (FP64) and writes it once.
+// CTA = 32 cells x K warps (lane = cell, warp = k1).  A persistent grid pulls (shell,
+// tile) items from a queue, largest shells first; each item accumulates the shell's
+// Q[k1, q1] in shared memory (FP64) and writes it once.
 #include <cuda_runtime.h>
+
 
 #include "wef_internal.hpp"
 
@@ -59,125 +60,32 @@ __device__ __forceinline__ double f2d_exact(float x) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// Thread mapping: lane = cell, warp w = the pair k1 = (2w, 2w + 1) (the second absent for
-// odd K in the last warp).  Two k1 per thread halve the per-pair loads of f[:, q3] and of
-// the pair records relative to one k1 per warp, which is what bounded the L1 pipe.
+// Thread mapping: lane = cell, warp = radial row k1 (K warps per CTA).  Each warp walks the
+// program on its own: per channel, per block of J q2 groups, stage 1 for the J groups
+// (core rows as float4, reused by the J groups), then the union of the block's q3: f[:, q3]
+// is loaded once and serves every q2 of the block it pairs with.
 template <int K>
 struct RfCfg {
-  static constexpr int KW = (K + 1) / 2;         // warps per CTA
-  static constexpr int KP4 = (K + 3) / 4 * 4;    // padded k2 (float4 core rows)
-  static constexpr int J = K <= 9 ? 4 : (K <= 13 ? 2 : 1);  // q2 groups per register block
-  // registers per thread that still let two CTAs share an SM (65536 / (2 * 32 * KW), in 8s)
-  static constexpr int MAXREG = (65536 / (64 * KW)) / 8 * 8 > 255 ? 255 : (65536 / (64 * KW)) / 8 * 8;
+  static constexpr int KP4 = (K + 3) / 4 * 4;  // padded k2 (float4 core rows)
+  static constexpr int J = rf_group_width(K);   // q2 groups per block (register budget)
+  // Registers per thread that let two CTAs share an SM: each of the 4 sub-partitions has
+  // 16384 registers and takes ceil(2 K / 4) of the two CTAs' warps.
+  static constexpr int WARPS_PER_SMSP = (2 * K + 3) / 4;
+  static constexpr int MAXREG_RAW = 16384 / (32 * WARPS_PER_SMSP) / 8 * 8;
+  static constexpr int MAXREG = MAXREG_RAW > 255 ? 255 : MAXREG_RAW;
 };
 
-// One symmetrised channel of one task: the channel's q2 groups in register blocks of J,
-// stage 1 (core rows as float4, reused by the J groups), then stage 2 and the FP64 Gaunt
-// reduction pair by pair.  TWO: this warp holds a second k1.
-template <int K, bool TWO>
-__device__ __forceinline__ void rf_channel(const int4 C, const float* __restrict__ ft, double2* __restrict__ acc,
-                                           const int4* __restrict__ outer, const int4* __restrict__ pairs,
-                                           const double2* __restrict__ pw, const float4* __restrict__ Ra) {
-  using Cfg = RfCfg<K>;
-  constexpr int J = Cfg::J, KP4 = Cfg::KP4, R4 = KP4 / 4;
-  constexpr int ACC_STRIDE = Cfg::KW * 32;
-  const float4* Rb = Ra + K * R4;  // next k1
-  for (int m0 = 0; m0 < C.z; m0 += J) {
-    const int nj = C.z - m0 < J ? C.z - m0 : J;
-    int4 M[J];
-    float fq[J][KP4];
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      M[j] = j < nj ? __ldg(outer + C.y + m0 + j) : make_int4(0, 0, 0, 0);
-#pragma unroll
-      for (int k2 = 0; k2 < KP4; ++k2) fq[j][k2] = (j < nj && k2 < K) ? __ldg(ft + (M[j].x * K + k2) * 32) : 0.0f;
-    }
-    // stage 1: A[j][t][k3] = sum_k2 Rt[k1_t][k2][k3] f[k2][q2_j]
-    float A[J][TWO ? 2 : 1][K];
-#pragma unroll
-    for (int k3 = 0; k3 < K; ++k3) {
-      float a0[J], a1[J];
-#pragma unroll
-      for (int j = 0; j < J; ++j) a0[j] = a1[j] = 0.0f;
-#pragma unroll
-      for (int c = 0; c < R4; ++c) {
-        const float4 ra = __ldg(Ra + k3 * R4 + c);
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-          a0[j] = fmaf(ra.x, fq[j][4 * c], a0[j]);
-          a0[j] = fmaf(ra.y, fq[j][4 * c + 1], a0[j]);
-          a0[j] = fmaf(ra.z, fq[j][4 * c + 2], a0[j]);
-          a0[j] = fmaf(ra.w, fq[j][4 * c + 3], a0[j]);
-        }
-        if (TWO) {
-          const float4 rb = __ldg(Rb + k3 * R4 + c);
-#pragma unroll
-          for (int j = 0; j < J; ++j) {
-            a1[j] = fmaf(rb.x, fq[j][4 * c], a1[j]);
-            a1[j] = fmaf(rb.y, fq[j][4 * c + 1], a1[j]);
-            a1[j] = fmaf(rb.z, fq[j][4 * c + 2], a1[j]);
-            a1[j] = fmaf(rb.w, fq[j][4 * c + 3], a1[j]);
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        A[j][0][k3] = a0[j];
-        if (TWO) A[j][TWO ? 1 : 0][k3] = a1[j];
-      }
-    }
-    // stage 2 + FP64 reduction, pair by pair
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      if (j >= nj) break;
-      for (int p = M[j].y; p < M[j].y + M[j].z; ++p) {
-        const int4 P = __ldg(pairs + p);  // q3, ne, q1a offset, q1b offset
-        const double2 W = __ldg(pw + p);
-        const float* f3 = ft + P.x * K * 32;
-        float b0 = 0.0f, b1 = 0.0f, c0 = 0.0f, c1 = 0.0f;
-#pragma unroll
-        for (int k3 = 0; k3 < K; ++k3) {
-          const float x = __ldg(f3 + k3 * 32);
-          if (k3 & 1) {
-            b1 = fmaf(A[j][0][k3], x, b1);
-            if (TWO) c1 = fmaf(A[j][TWO ? 1 : 0][k3], x, c1);
-          } else {
-            b0 = fmaf(A[j][0][k3], x, b0);
-            if (TWO) c0 = fmaf(A[j][TWO ? 1 : 0][k3], x, c0);
-          }
-        }
-        const double Ba = f2d_exact(b0 + b1);
-        const double Bb = TWO ? f2d_exact(c0 + c1) : 0.0;
-        double2* pa = acc + P.z * ACC_STRIDE;
-        double2 v = *pa;
-        v.x = fma(W.x, Ba, v.x);
-        if (TWO) v.y = fma(W.x, Bb, v.y);
-        *pa = v;
-        if (P.y > 1) {
-          double2* pb = acc + P.w * ACC_STRIDE;
-          v = *pb;
-          v.x = fma(W.y, Ba, v.x);
-          if (TWO) v.y = fma(W.y, Bb, v.y);
-          *pb = v;
-        }
-      }
-    }
-  }
-}
-
 template <int K>
-__global__ void __launch_bounds__(32 * RfCfg<K>::KW) __maxnreg__(RfCfg<K>::MAXREG)
+__global__ void __launch_bounds__(32 * K) __maxnreg__(RfCfg<K>::MAXREG)
     rf_kernel(const float* __restrict__ ftile, double* __restrict__ qout, int64_t ncells, int64_t ntiles, int NQ,
-              const int4* __restrict__ tasks, const int4* __restrict__ chans, const int4* __restrict__ outer,
-              const int4* __restrict__ pairs, const double2* __restrict__ pw, const int32_t* __restrict__ order,
-              int ntasks, const float* __restrict__ R32, int* __restrict__ queue) {
+              const int4* __restrict__ tasks, const int4* __restrict__ chans, const int4* __restrict__ blocks,
+              const int4* __restrict__ uents, const int4* __restrict__ pairs, const double2* __restrict__ pw,
+              const int32_t* __restrict__ order, int ntasks, const float* __restrict__ R32, int* __restrict__ queue) {
   using Cfg = RfCfg<K>;
-  constexpr int ACC_STRIDE = Cfg::KW * 32, K1P = 2 * Cfg::KW;
-  extern __shared__ double2 qacc[];  // [m1][w][32]: (k1 = 2w, k1 = 2w + 1)
+  constexpr int J = Cfg::J, KP4 = Cfg::KP4, R4 = KP4 / 4, S = K * 32;
+  extern __shared__ double qacc[];  // [m1][k1][32]
   __shared__ int item_s;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k1a = 2 * w;
-  const bool two = k1a + 1 < K;
+  const int k1 = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nitems = ntiles * ntasks;
   for (;;) {
     if (threadIdx.x == 0) item_s = atomicAdd(queue, 1);
@@ -189,25 +97,79 @@ __global__ void __launch_bounds__(32 * RfCfg<K>::KW) __maxnreg__(RfCfg<K>::MAXRE
     const int64_t tile = it % ntiles;
     const int4 T = __ldg(tasks + task);  // q1_base, n1, chan_start, nchan
     const float* ft = ftile + tile * (int64_t)NQ * K * 32 + lane;
-    double2* acc = qacc + w * 32 + lane;
-    for (int m = 0; m < T.y; ++m) acc[m * ACC_STRIDE] = make_double2(0.0, 0.0);
+    double* acc = qacc + k1 * 32 + lane;
+    for (int m = 0; m < T.y; ++m) acc[m * S] = 0.0;
     for (int ch = T.z; ch < T.z + T.w; ++ch) {
-      const int4 C = __ldg(chans + ch);  // sc, outer_start, n_outer
-      const float4* Ra = reinterpret_cast<const float4*>(R32 + ((int64_t)C.x * K1P + k1a) * K * Cfg::KP4);
-      if (two)
-        rf_channel<K, true>(C, ft, acc, outer, pairs, pw, Ra);
-      else
-        rf_channel<K, false>(C, ft, acc, outer, pairs, pw, Ra);
+      const int4 C = __ldg(chans + ch);  // sc, blk_start, nblk
+      const float4* Ra = reinterpret_cast<const float4*>(R32 + ((int64_t)C.x * K + k1) * K * KP4);  // [k3][k2]
+      for (int b = C.y; b < C.y + C.z; ++b) {
+        const int4 B0 = __ldg(blocks + 2 * b), B1 = __ldg(blocks + 2 * b + 1);  // {nj, u_start, nu}, q2s
+        const int nj = B0.x;
+        const int q2v[4] = {B1.x, B1.y, B1.z, B1.w};
+        float fq[J][KP4];
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+          for (int k2 = 0; k2 < KP4; ++k2) fq[j][k2] = (j < nj && k2 < K) ? __ldg(ft + (q2v[j] * K + k2) * 32) : 0.0f;
+        // stage 1: A[j][k3] = sum_k2 Rt[k1][k2][k3] f[k2][q2_j]
+        float A[J][K];
+#pragma unroll
+        for (int k3 = 0; k3 < K; ++k3) {
+          float a[J];
+#pragma unroll
+          for (int j = 0; j < J; ++j) a[j] = 0.0f;
+#pragma unroll
+          for (int c = 0; c < R4; ++c) {
+            const float4 r = __ldg(Ra + k3 * R4 + c);
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+              a[j] = fmaf(r.x, fq[j][4 * c], a[j]);
+              a[j] = fmaf(r.y, fq[j][4 * c + 1], a[j]);
+              a[j] = fmaf(r.z, fq[j][4 * c + 2], a[j]);
+              a[j] = fmaf(r.w, fq[j][4 * c + 3], a[j]);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < J; ++j) A[j][k3] = a[j];
+        }
+        // stage 2 + FP64 reduction over the union of the block's q3
+        for (int u = B0.y; u < B0.y + B0.z; ++u) {
+          const int4 U = __ldg(uents + u);  // q3, mask, pair_start
+          const float* f3 = ft + U.x * K * 32;
+          // J = 1 (large K, tight registers): consume f[:, q3] as it arrives
+          float x[J > 1 ? K : 1];
+          if constexpr (J > 1) {
+#pragma unroll
+            for (int k3 = 0; k3 < K; ++k3) x[k3] = __ldg(f3 + k3 * 32);
+          }
+          int p = U.z;
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            if (!((U.y >> j) & 1)) continue;
+            float b0 = 0.0f, b1 = 0.0f;
+#pragma unroll
+            for (int k3 = 0; k3 < K; ++k3) {
+              const float xv = J > 1 ? x[J > 1 ? k3 : 0] : __ldg(f3 + k3 * 32);
+              if (k3 & 1) b1 = fmaf(A[j][k3], xv, b1);
+              else b0 = fmaf(A[j][k3], xv, b0);
+            }
+            const double Bv = f2d_exact(b0 + b1);
+            const int4 P = __ldg(pairs + p);  // ne, q1a offset, q1b offset
+            const double2 W = __ldg(pw + p);
+            ++p;
+            acc[P.y * S] = fma(W.x, Bv, acc[P.y * S]);
+            if (P.x > 1) acc[P.z * S] = fma(W.y, Bv, acc[P.z * S]);
+          }
+        }
+      }
     }
     const int64_t cell = tile * 32 + lane;
     if (cell < ncells) {
-      double* qc = qout + cell * (int64_t)K * NQ + (int64_t)k1a * NQ + T.x;
+      double* qc = qout + cell * (int64_t)K * NQ + (int64_t)k1 * NQ + T.x;
       for (int m = 0; m < T.y; ++m) {
         const int q1 = T.x + m;
-        const double2 v = acc[m * ACC_STRIDE];
         // conservation projection: (k1 = 0, q1 = 0..3) and (k1 = 1, q1 = 0) are zero
-        qc[m] = (k1a == 0 && q1 < 4) ? 0.0 : v.x;
-        if (two) qc[NQ + m] = (k1a == 0 && q1 == 0) ? 0.0 : v.y;
+        qc[m] = ((k1 == 0 && q1 < 4) || (k1 == 1 && q1 == 0)) ? 0.0 : acc[m * S];
       }
     }
     __syncthreads();
@@ -218,9 +180,9 @@ template <int K>
 cudaError_t launch_rf_k(const double* f, float* ftile32, int* queue, double* q, int64_t ncells, int NQ,
                         const DevRadial& r, const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0,
                         cudaEvent_t ev1) {
-  constexpr int threads = 32 * RfCfg<K>::KW;
+  constexpr int threads = 32 * K;
   const int64_t ntiles = (ncells + 31) / 32;
-  const size_t smem = (size_t)r.n1max * threads * sizeof(double2);
+  const size_t smem = (size_t)r.n1max * threads * sizeof(double);
   static size_t attr = 0;  // dynamic shared memory opted in so far for this instantiation
   if (smem > attr) {
     cudaError_t e = cudaFuncSetAttribute(rf_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -238,8 +200,8 @@ cudaError_t launch_rf_k(const double* f, float* ftile32, int* queue, double* q, 
   int64_t grid = (int64_t)nsm * per_sm;
   if (grid > nitems) grid = nitems;
   if (ev0) cudaEventRecord(ev0, s);
-  rf_kernel<K><<<(unsigned)grid, threads, smem, s>>>(ftile32, q, ncells, ntiles, NQ, r.tasks, r.chans, r.outer,
-                                                     r.pairs, r.pw, r.order, r.ntasks, R32, queue);
+  rf_kernel<K><<<(unsigned)grid, threads, smem, s>>>(ftile32, q, ncells, ntiles, NQ, r.tasks, r.chans, r.blocks,
+                                                     r.uents, r.pairs, r.pw, r.order, r.ntasks, R32, queue);
   if (ev1) cudaEventRecord(ev1, s);
   return cudaGetLastError();
 }

@@ -24,16 +24,32 @@ struct wef_operator {
   } dp[2];
   int* d_status = nullptr;  // set by kernels whose bounded waits gave up
   // radial-first program
-  int32_t *r_tasks = nullptr, *r_chans = nullptr, *r_outer = nullptr, *r_pairs = nullptr, *r_order = nullptr;
+  int32_t *r_tasks = nullptr, *r_chans = nullptr, *r_blocks = nullptr, *r_uents = nullptr, *r_pairs = nullptr, *r_order = nullptr;
   double* r_pw = nullptr;
   // core
   double* d_R64 = nullptr;      // symmetrised core [sc][k3][k1][k2]
   uint8_t* d_Bbf16 = nullptr;   // packed MMA B tiles, BF16
   uint8_t* d_Btf32 = nullptr;   // packed MMA B tiles, TF32
-  float* d_R32 = nullptr;       // symmetrised core, FP32 [sc][K1P][k3][KP4] (radial-first path)
+  float* d_R32 = nullptr;       // symmetrised core, FP32 [sc][k1][k3][KP4] (radial-first path)
   bool has_core = false;
   // tracing
   cudaEvent_t trace_start = nullptr, trace_stop = nullptr;
+  // baselines (naive COO, dense tensor): symmetrised entries sorted by q1, cuBLAS handle
+  void* b_ent = nullptr;
+  double* b_w = nullptr;
+  int32_t* b_off = nullptr;
+  int64_t b_nent = 0;
+  void* cublas = nullptr;
+
+  void release_baselines() {
+    cudaFree(b_ent);
+    cudaFree(b_w);
+    cudaFree(b_off);
+    b_ent = nullptr;
+    b_w = nullptr;
+    b_off = nullptr;
+    b_nent = 0;
+  }
 
   void release_core() {
     cudaFree(d_R64);
@@ -56,12 +72,13 @@ struct wef_operator {
     }
     cudaFree(d_status);
     d_status = nullptr;
-    for (int32_t** pp : {&r_tasks, &r_chans, &r_outer, &r_pairs, &r_order}) {
+    for (int32_t** pp : {&r_tasks, &r_chans, &r_blocks, &r_uents, &r_pairs, &r_order}) {
       cudaFree(*pp);
       *pp = nullptr;
     }
     cudaFree(r_pw);
     r_pw = nullptr;
+    release_baselines();
     release_core();
   }
 };

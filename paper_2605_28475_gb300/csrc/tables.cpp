@@ -266,11 +266,13 @@ std::string build_tables(int kmax, int lmax, Tables& t) {
       if (i == 0 || v[i].q2 != v[i - 1].q2) ++t.n_sym_groups;
   }
   // Radial-first program: per shell, per channel, group the channel's entries by q2,
-  // then by q3; each (q2, q3) pair feeds at most two q1 of the shell.
+  // then by q3; each (q2, q3) pair feeds at most two q1 of the shell.  Blocks of J q2
+  // groups list the union of their q3 with a membership mask.
   {
     RadialProgram& RP = t.rprog;
     RP = RadialProgram();
-    const int K = t.K;
+    const int K = t.K, J = rf_group_width(K);
+    RP.J = J;
     for (int l1 = 0; l1 <= lmax; ++l1) {
       const int q1b = l1 * l1, n1 = 2 * l1 + 1;
       RP.n1max = std::max(RP.n1max, n1);
@@ -279,33 +281,43 @@ std::string build_tables(int kmax, int lmax, Tables& t) {
       double cost = 0.0;
       for (int sc = 0; sc < NS; ++sc) {
         if (t.chans[t.sym_chan[sc]].l1 != l1) continue;
-        // (q2, q3) -> list of (q1 offset, w)
-        std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> byp;
+        // q2 -> q3 -> list of (q1 offset, w)
+        std::map<int, std::map<int, std::vector<std::pair<int, double>>>> byp;
         for (int m = 0; m < n1; ++m)
-          for (const Entry& e : sl[(size_t)sc * t.NQ + q1b + m]) byp[{e.q2, e.q3}].push_back({m, e.w});
+          for (const Entry& e : sl[(size_t)sc * t.NQ + q1b + m]) byp[e.q2][e.q3].push_back({m, e.w});
         if (byp.empty()) continue;
-        const int ms = (int)RP.outer.size() / 4;
-        int nm3 = 0, cur_q2 = -1;
-        for (const auto& kv : byp) {
-          const int q2 = kv.first.first, q3 = kv.first.second;
-          if (q2 != cur_q2) {
-            RP.outer.insert(RP.outer.end(), {q2, (int32_t)(RP.pairs.size() / 4), 0, 0});
-            cur_q2 = q2;
-            ++nm3;
-            cost += 2.0 * K * K * K;
+        std::vector<int> q2s;
+        for (const auto& kv : byp) q2s.push_back(kv.first);
+        const int bs = (int)RP.blocks.size() / 8;
+        int nblk = 0;
+        for (size_t b0 = 0; b0 < q2s.size(); b0 += J) {
+          const int nj = (int)std::min<size_t>(J, q2s.size() - b0);
+          std::map<int, int> mask;  // q3 -> bits
+          for (int j = 0; j < nj; ++j)
+            for (const auto& kv : byp[q2s[b0 + j]]) mask[kv.first] |= 1 << j;
+          RP.blocks.insert(RP.blocks.end(), {nj, (int32_t)(RP.uents.size() / 4), (int32_t)mask.size(), 0});
+          for (int j = 0; j < 4; ++j) RP.blocks.push_back(j < nj ? q2s[b0 + j] : 0);
+          for (const auto& mk : mask) {
+            const int q3 = mk.first;
+            RP.uents.insert(RP.uents.end(), {q3, mk.second, (int32_t)(RP.pairs.size() / 4), 0});
+            for (int j = 0; j < nj; ++j) {
+              if (!(mk.second >> j & 1)) continue;
+              const auto& v = byp[q2s[b0 + j]][q3];
+              if (v.size() > 2) return "a radial-first pair feeding more than two q1";
+              RP.pairs.insert(RP.pairs.end(), {(int32_t)v.size(), v[0].first, v.size() > 1 ? v[1].first : v[0].first, 0});
+              RP.pw.push_back(v[0].second);
+              RP.pw.push_back(v.size() > 1 ? v[1].second : 0.0);
+              cost += 2.0 * K * K + 2.0 * K * (double)v.size();
+              RP.fp32_flops += 2.0 * K * K;
+              RP.fp64_flops += 2.0 * K * (double)v.size();
+            }
           }
-          const auto& v = kv.second;
-          if (v.size() > 2) return "a radial-first pair feeding more than two q1";
-          RP.pairs.insert(RP.pairs.end(), {q3, (int32_t)v.size(), v[0].first, v.size() > 1 ? v[1].first : v[0].first});
-          RP.pw.push_back(v[0].second);
-          RP.pw.push_back(v.size() > 1 ? v[1].second : 0.0);
-          RP.outer[RP.outer.size() - 2] += 1;
-          cost += 2.0 * K * K + 2.0 * K * (double)v.size();
-          RP.fp32_flops += 2.0 * K * K;
-          RP.fp64_flops += 2.0 * K * (double)v.size();
+          cost += 2.0 * K * K * K * nj;
+          RP.fp32_flops += 2.0 * K * K * K * nj;
+          RP.n_groups += nj;
+          ++nblk;
         }
-        RP.fp32_flops += 2.0 * K * K * K * nm3;
-        RP.chans.insert(RP.chans.end(), {sc, ms, nm3, 0});
+        RP.chans.insert(RP.chans.end(), {sc, bs, nblk, 0});
         ++nch;
       }
       RP.tasks.insert(RP.tasks.end(), {q1b, n1, cs, nch});

@@ -40,22 +40,37 @@ struct Program {
   int ntasks() const { return (int)task_cost.size(); }
 };
 
+#ifdef __CUDACC__
+#define WEF_HD __host__ __device__
+#else
+#define WEF_HD
+#endif
+
+// q2 groups the radial-first kernel keeps in registers at once (its register budget).
+WEF_HD constexpr int rf_group_width(int K) { return K <= 9 ? 4 : (K <= 13 ? 2 : 1); }
+
 // Radial-first program (paper Sec. 4.5.3 ordering with a dense two-stage radial
 // contraction).  One task per output shell l1:
 //   tasks:  {q1_base, n1, chan_start, nchan}
-//   chans:  {sc, outer_start, n_outer, 0}  symmetrised channel (l2 <= l3) and its q2 groups
-//   outer:  {q2, pair_start, npairs, 0}    one group per q2 used by the channel
-//   pairs:  {q3, ne, q1a - q1_base, q1b - q1_base}, weights pw {ga, gb} (gb = 0 if ne = 1)
+//   chans:  {sc, blk_start, nblk, 0}        symmetrised channel (l2 <= l3)
+//   blocks: two int4 per block: {nj, u_start, nu, 0}, {q2_0, q2_1, q2_2, q2_3}: up to
+//           J = rf_group_width(K) of the channel's q2 (the smaller shell), whose stage-1
+//           products A(q2_j) are held together
+//   uents:  {q3, mask, pair_start, 0}: each q3 paired with any q2 of the block, once; bit j
+//           of mask set if (q2_j, q3) is a pair; its pairs follow in j order
+//   pairs:  {ne, q1a - q1_base, q1b - q1_base, 0}, weights pw {ga, gb} (gb = 0 if ne = 1)
 // order:  task indices by decreasing cost (the persistent kernel's schedule).
-// Grouping by q2, the smaller shell of the symmetrised channel, makes the first radial
-// stage (2K^3 flops per group) run over 4067 instead of 6125 groups at K = L = 12.
+// Grouping by q2 makes stage 1 (2K^3 flops per q2 group) run over 4067 instead of 6125
+// groups at K = L = 12; walking the union of the block's q3 loads each f[:, q3] once per
+// block instead of once per pair (32707 instead of 56981 loads of K values for J = 2).
 struct RadialProgram {
-  std::vector<int32_t> tasks, chans, outer, pairs;
+  std::vector<int32_t> tasks, chans, blocks, uents, pairs;
   std::vector<double> pw;
   std::vector<int32_t> order;
   std::vector<double> task_cost;  // FP64 + FP32 flops per cell, for the schedule
   double fp64_flops = 0.0, fp32_flops = 0.0;
-  int n1max = 1;
+  int n1max = 1, J = 1;
+  int64_t n_groups = 0;  // q2 groups (stage-1 products) over all tasks
 };
 
 struct Tables {

@@ -73,7 +73,8 @@ cudaError_t ensure_device(wef_operator* op) {
   const RadialProgram& RP = op->T.rprog;
   if (e == cudaSuccess) e = upload(&op->r_tasks, RP.tasks);
   if (e == cudaSuccess) e = upload(&op->r_chans, RP.chans);
-  if (e == cudaSuccess) e = upload(&op->r_outer, RP.outer);
+  if (e == cudaSuccess) e = upload(&op->r_blocks, RP.blocks);
+  if (e == cudaSuccess) e = upload(&op->r_uents, RP.uents);
   if (e == cudaSuccess) e = upload(&op->r_pairs, RP.pairs);
   if (e == cudaSuccess) e = upload(&op->r_pw, RP.pw);
   if (e == cudaSuccess) e = upload(&op->r_order, RP.order);
@@ -180,16 +181,15 @@ wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigne
       tc_pack_b_tile(K, true, Rt.data(), &Bt[(size_t)s * nt]);
     }
   }
-  // FP32 copy for the radial-first path, layout [sc][k1 -> K1P][k3][k2 -> KP4]: k2, the
-  // index the first radial stage contracts, fastest and padded to whole float4s; k1 padded
-  // to an even count (two k1 per thread); pads are zero.
-  const int K1P = rf_k1_padded(K), KP4 = rf_k2_padded(K);
-  std::vector<float> R32((size_t)NS * K1P * K * KP4, 0.0f);
+  // FP32 copy for the radial-first path, layout [sc][k1][k3][k2 -> KP4]: k2, the index the
+  // first radial stage contracts, fastest and padded with zeros to whole float4s.
+  const int KP4 = rf_k2_padded(K);
+  std::vector<float> R32((size_t)NS * K * K * KP4, 0.0f);
   for (int s = 0; s < NS; ++s)
     for (int k1 = 0; k1 < K; ++k1)
       for (int k2 = 0; k2 < K; ++k2)
         for (int k3 = 0; k3 < K; ++k3)
-          R32[(((size_t)s * K1P + k1) * K + k3) * KP4 + k2] = (float)R64[(((size_t)s * K + k3) * K + k1) * K + k2];
+          R32[(((size_t)s * K + k1) * K + k3) * KP4 + k2] = (float)R64[(((size_t)s * K + k3) * K + k1) * K + k2];
   op->release_core();
   cudaError_t e = upload(&op->d_R64, R64);
   if (e == cudaSuccess) e = upload(&op->d_R32, R32);
@@ -232,8 +232,9 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
   const int K = op->T.K, NQ = op->T.NQ;
   if (prec == WEF_RADIAL_FP32) {
     const RadialProgram& RP = op->T.rprog;
-    DevRadial r{(const int4*)op->r_tasks, (const int4*)op->r_chans, (const int4*)op->r_outer, (const int4*)op->r_pairs,
-                (const double2*)op->r_pw, op->r_order, (int)RP.task_cost.size(), RP.n1max};
+    DevRadial r{(const int4*)op->r_tasks, (const int4*)op->r_chans, (const int4*)op->r_blocks,
+                (const int4*)op->r_uents, (const int4*)op->r_pairs, (const double2*)op->r_pw, op->r_order,
+                (int)RP.task_cost.size(), RP.n1max};
     cudaError_t er = launch_rf(K, f_dev, (float*)((char*)workspace + 256), (int*)workspace, q_dev, ncells, NQ, r,
                                op->d_R32, op->sms, s, op->trace_start, op->trace_stop);
     if (er != cudaSuccess) return cuda_fail(er, "wef_evaluate: radial-first kernels");
@@ -321,6 +322,7 @@ wef_status wef_device_status(wef_op op, int reset) {
 
 wef_status wef_destroy(wef_op op) {
   if (!op) return WEF_OK;
+  if (op->cublas) wef::destroy_cublas(op->cublas);
   op->release();
   delete op;
   return WEF_OK;

@@ -25,7 +25,8 @@ constexpr int kCellsPerTile = 32;
 struct DevRadial {
   const int4* tasks = nullptr;
   const int4* chans = nullptr;
-  const int4* outer = nullptr;
+  const int4* blocks = nullptr;
+  const int4* uents = nullptr;
   const int4* pairs = nullptr;
   const double2* pw = nullptr;
   const int32_t* order = nullptr;
@@ -33,8 +34,10 @@ struct DevRadial {
   int n1max = 1;
 };
 
-// Radial-first core layout: k1 padded to an even count, k2 to whole float4s.
-inline int rf_k1_padded(int K) { return (K + 1) / 2 * 2; }
+// Releases the cuBLAS handle of the dense baseline.
+void destroy_cublas(void* handle);
+
+// Radial-first FP32 core layout [sc][k1][k3][k2 -> KP4]: k2 padded to whole float4s.
 inline int rf_k2_padded(int K) { return (K + 3) / 4 * 4; }
 
 // Radial-first evaluation: FP32 re-tiling of f, then the persistent radial-first
