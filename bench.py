@@ -219,7 +219,7 @@ def bench_small(args, W, torch, dev, world, kind):
     else:
         km, gamma, n, f_host = 8, 1.0, 4096, wi.two_maxwellians(8, 8, 4096, seed=2, pool=1024)
     op = W.Operator(km, km, gamma)
-    op.upload_core(op.build_core())
+    op.upload_core(op.build_core(device=True))
     f = torch.from_numpy(f_host).to(dev)
     q = torch.empty_like(f)
     st = torch.cuda.current_stream(dev)
@@ -247,7 +247,7 @@ def bench_baselines(args, W, torch, dev, world):
 
     km = 8
     op = W.Operator(km, km, 1.0)
-    op.upload_core(op.build_core())
+    op.upload_core(op.build_core(device=True))
     st = torch.cuda.current_stream(dev)
     n_fact, n_dense = 4096, 256
     f_host = wi.two_maxwellians(km, km, n_fact, seed=2, pool=1024)
@@ -293,7 +293,7 @@ def bench_ragged(args, W, torch, dev, world, ncells=32768, seed=4):
     real = os.environ.get("WEF_BENCH_QUADRATURE_CORES") == "1"
     for i, ((km, lm), n) in enumerate(zip(shapes, counts)):
         op = W.Operator(km, lm, 0.5)
-        R = op.build_core() if real else wi.random_core(op.n_channels, km, seed=100 + i)
+        R = op.build_core(device=True) if real else wi.random_core(op.n_channels, km, seed=100 + i)
         op.upload_core(R)
         ops.append(op)
         fs.append(wi.two_maxwellians(km, lm, n, seed=200 + i, pool=min(256, max(n, 1))).reshape(-1))
@@ -330,7 +330,7 @@ def bench_serve(args, W, torch, dev, world):
     ops = {}
     for i, (km, lm) in enumerate(shapes):
         op = W.Operator(km, lm, 1.0)
-        op.upload_core(op.build_core() if real else wi.random_core(op.n_channels, km, seed=300 + i))
+        op.upload_core(op.build_core(device=True) if real else wi.random_core(op.n_channels, km, seed=300 + i))
         ops[(km, lm)] = op
     # capacity: full-batch throughput per shape at the serving precision
     prec = W.PRECISIONS[args.precision]
@@ -392,7 +392,7 @@ def main():
         return
     probe = fp64_probe() if rank == 0 else None
     op = W.Operator(KMAX, LMAX, GAMMA)
-    R = op.build_core()
+    R = op.build_core(device=True)  # the library quadrature, assembled on the GPU
     op.upload_core(R)
     ncells = args.ncells
     f_host = inputs(ncells, seed=3 + rank)
