@@ -38,6 +38,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA pipe: 2 DFMA lanes per SM per clock on GB300 (measured: 1.20 TFLOP/s at
 # 1987 MHz with full warps), x 152 SMs x 2 flops x 2070 MHz maximum clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM bytes (read + write) of one launch of the dominant kernel at the default workload
+# (K=L=12, 16384 cells), from a one-pass ncu capture of `bench.py --steps 1 --warmup 1
+# --precision rf32` (dram__bytes_read.sum 411.99 MB + dram__bytes_write.sum 328.73 MB).
+TRAFFIC_BYTES = {"rf32": 740.72e6}
 
 
 def parse():
@@ -50,11 +54,13 @@ def parse():
     ap.add_argument("--ncells", type=int, default=NCELLS)
     ap.add_argument("--cpu-sample-rows", type=int, default=384)
     ap.add_argument("--cpu-sample-cells", type=int, default=4)
-    ap.add_argument("--workload", default="kl12", choices=["kl12", "maxwell4", "hs8", "ragged", "serve", "baselines"],
+    ap.add_argument("--workload", default="kl12",
+                    choices=["kl12", "maxwell4", "hs8", "ragged", "serve", "baselines", "rk4", "core"],
                     help="kl12: hard spheres K=L=12 x 16384 cells (default); maxwell4: one Maxwell cell at "
                          "K=L=4; hs8: hard spheres K=L=8 x 4096 cells; ragged: VHS, 32768 cells with "
                          "(Kmax, Lmax) drawn from {6,8,10,12,16}; serve: Poisson request stream; baselines: "
-                         "factorised vs naive-COO vs dense tensor at K=L=8")
+                         "factorised vs naive-COO vs dense tensor at K=L=8; rk4: device RK4 and linearized "
+                         "products at K=L=12; core: GPU vs host assembly of the core at K=L=12")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     return ap.parse_args()
 
@@ -230,8 +236,34 @@ def bench_small(args, W, torch, dev, world, kind):
     wl = ("Maxwell molecules, Kmax=Lmax=4, 1 perturbed-Maxwellian cell, FP64" if kind == "maxwell4" else
           "hard spheres, Kmax=Lmax=8, 4096 two-Maxwellian cells, FP64")
     if kind == "maxwell4":
-        return _line("Q(f,f) latency, 1 cell, K=L=4", ms * 1e3, "us", ms, args, world, "f64", wl, hib=False,
-                     fp64_flops_per_cell=fp64_flops)
+        # device latency: 50 evaluations captured back to back in one CUDA graph, replayed
+        reps = 50
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            cs = torch.cuda.current_stream(dev).cuda_stream
+            for _ in range(reps):
+                W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), n, 0, ws.data_ptr(), ws.numel(), cs)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(max(args.steps, 5)):
+            g.replay()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        dev_us = e0.elapsed_time(e1) * 1e3 / (max(args.steps, 5) * reps)
+        # what a caller sees: one synchronous call (launch from Python + wait), median
+        wall = []
+        for _ in range(200):
+            t0 = time.perf_counter()
+            step()
+            st.synchronize()
+            wall.append(time.perf_counter() - t0)
+        return _line("Q(f,f) latency, 1 cell, K=L=4", dev_us, "us", dev_us / 1e3, args, world, "f64", wl, hib=False,
+                     fp64_flops_per_cell=fp64_flops, latency_note="device time per evaluation (graph of 50 back-to-back "
+                     "evaluations, replayed)", sync_call_us_median=1e6 * statistics.median(wall),
+                     queued_call_us=ms * 1e3, gpu_launches=2 * reps * max(args.steps, 5))
     return _line("Q(f,f) cell-evals/s at K=L=8", n / (ms / 1e3), "cells/s", ms, args, world, "f64", wl,
                  roofline={"bound": "alu", "achieved": fp64_flops * n / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                            "unit": "TFLOP/s", "frac": fp64_flops * n / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
@@ -277,6 +309,55 @@ def bench_baselines(args, W, torch, dev, world):
                  flops_per_cell={"dense": 2.0 * N**3, "naive_coo": n_sym * 2.0 * (K**3 + K**2 + K),
                                  "fp64": W.wef_flops(op.h, 0)[0], "rf32_fp64": W.wef_flops(op.h, rfp)[0],
                                  "rf32_fp32": W.wef_flops(op.h, rfp)[1]})
+
+
+def bench_rk4(args, W, torch, dev, world, ncells=16384, nrk=4):
+    """Time integration on the device: RK4 steps of df/dt = Q(f, f) for every cell (four
+    evaluations per step), hard spheres, Kmax=Lmax=12, two-Maxwellian cells; and linearized
+    products L d at per-cell base states (three evaluations each)."""
+    import wef_inputs as wi
+
+    op = W.Operator(KMAX, LMAX, GAMMA)
+    op.upload_core(op.build_core(device=True))
+    f0 = torch.from_numpy(inputs(ncells, seed=3)).to(dev)
+    f = f0.clone()
+    d = torch.from_numpy(wi.random_cells(KMAX, LMAX, ncells, seed=9)).to(dev)
+    st = torch.cuda.current_stream(dev)
+    prec = W.PRECISIONS[args.precision]
+    step = lambda: op.integrate(f, 1e-3, nrk, precision=prec)  # noqa: E731
+    ms = _time_steps(step, args.steps, args.warmup, st, torch)
+    out = torch.empty_like(d)
+    lstep = lambda: op.linearized_apply(f0, d, out, precision=prec)  # noqa: E731
+    ms_l = _time_steps(lstep, args.steps, args.warmup, st, torch)
+    dtype = "f64" if args.precision == "fp64" else f"f64+{args.precision}"
+    return _line("RK4 cell-steps/s at K=L=12", ncells * nrk / (ms / 1e3), "cell-steps/s", ms, args, world, dtype,
+                 f"hard spheres, Kmax=Lmax=12, {ncells} two-Maxwellian cells, {nrk} RK4 steps (dt=1e-3) per timed "
+                 f"step, {args.precision} evaluations",
+                 evaluations_per_s=4 * ncells * nrk / (ms / 1e3),
+                 linearized_products_per_s=ncells / (ms_l / 1e3))
+
+
+def bench_core(args, W, torch, dev, world):
+    """Assembly of the kinematic core (Sec. 4.3, Appendix A-B) at Kmax=Lmax=12, hard spheres,
+    paddings 20/20: on the GPU (FP64) against the host builder on all host cores."""
+    op = W.Operator(KMAX, LMAX, GAMMA)
+    op.build_core(device=True)  # warm-up (context, module load)
+    t = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        Rd = op.build_core(device=True)
+        t.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    Rh = op.build_core()
+    th = time.perf_counter() - t0
+    sec = statistics.median(t)
+    K = KMAX + 1
+    # radial points x channels x K^3 FMAs (the dominant contraction), 2 flops each
+    return _line("core assembly seconds at K=L=12", sec, "s", sec * 1e3, args, world, "f64",
+                 "hard spheres, Kmax=Lmax=12, 616 channels, paddings 20/20, GPU assembly (median of runs) vs the host "
+                 "builder on all host cores", hib=False, host_seconds=th, host_cores=os.cpu_count(),
+                 max_rel_diff=float(np.max(np.abs(Rd - Rh)) / np.max(np.abs(Rh))), K=K)
 
 
 def bench_ragged(args, W, torch, dev, world, ncells=32768, seed=4):
@@ -352,12 +433,16 @@ def bench_serve(args, W, torch, dev, world):
     rate = 0.7 / mean_service
     reqs = serve.poisson_requests(rate, args.duration, shapes, max_cells, seed=5,
                                   make_cells=lambda sh, n, s: wi.random_cells(sh[0], sh[1], n, seed=s))
-    srv = serve.Server(ops, arena_bytes=24 << 30, nslots=8, precision=args.precision, device=str(dev))
+    # batches capped at ~50 ms of estimated GPU time so that small requests do not queue
+    # behind one huge batch (a single larger request still goes alone)
+    srv = serve.Server(ops, arena_bytes=24 << 30, nslots=8, precision=args.precision, device=str(dev),
+                       cost_per_cell={sh: 1.0 / c for sh, c in cap.items()}, max_batch_s=0.05)
     res = serve.run(srv, reqs)
     dtype = "f64" if args.precision == "fp64" else f"f64+{args.precision}"
     return _line("serve: p50/p99 latency and cells/s", res["cells_per_s"], "cells/s", None, args, world, dtype,
                  f"Poisson arrivals at 0.7x capacity ({rate:.1f} req/s) for {args.duration:.0f} s; sizes log-uniform "
-                 f"1-{max_cells} cells; Kmax=Lmax in {{8,10,12,16}}; 8 stream slots; 24 GiB admission arena",
+                 f"1-{max_cells} cells; Kmax=Lmax in {{8,10,12,16}}; 8 stream slots; 24 GiB admission arena; "
+                 f"batches capped at 50 ms of estimated GPU time",
                  serving=res, capacity_cells_per_s={f"{k[0]}x{k[1]}": v for k, v in cap.items()})
 
 
@@ -383,7 +468,9 @@ def main():
               "hs8": lambda: bench_small(args, W, torch, dev, world, "hs8"),
               "ragged": lambda: bench_ragged(args, W, torch, dev, world),
               "serve": lambda: bench_serve(args, W, torch, dev, world),
-              "baselines": lambda: bench_baselines(args, W, torch, dev, world)}[args.workload]
+              "baselines": lambda: bench_baselines(args, W, torch, dev, world),
+              "rk4": lambda: bench_rk4(args, W, torch, dev, world),
+              "core": lambda: bench_core(args, W, torch, dev, world)}[args.workload]
         line = fn()
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -455,20 +542,26 @@ def main():
         variants[pr] = measure(pr, with_clocks=(pr == args.precision))
     head = variants[args.precision]
     step = head["step"]
-    # end to end through the public API: pinned host f -> device, evaluate, Q -> pinned host
+    # end to end through the C ABI with host buffers: wef_evaluate_host streams pinned f to
+    # the device in chunks and Q back, the copies of one chunk overlapping the evaluation of
+    # the next; every byte of f in and Q out crosses host<->device inside the timed region
     f_pin = torch.from_numpy(f_host).pin_memory()
     q_pin = torch.empty_like(f_pin).pin_memory()
+    prec_h = W.PRECISIONS[args.precision]
+    chunk = 4096
+    hws = torch.empty(W.wef_host_workspace_size(op.h, chunk, prec_h), dtype=torch.uint8, device=dev)
+
+    def host_step():
+        W.wef_evaluate_host(op.h, f_pin.data_ptr(), q_pin.data_ptr(), ncells, chunk, prec_h, hws.data_ptr(),
+                            hws.numel(), stream.cuda_stream)
+
     for _ in range(2):
-        f.copy_(f_pin, non_blocking=True)
-        step()
-        q_pin.copy_(q, non_blocking=True)
+        host_step()
     torch.cuda.synchronize(dev)
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a0.record(stream)
     for _ in range(args.steps):
-        f.copy_(f_pin, non_blocking=True)
-        step()
-        q_pin.copy_(q, non_blocking=True)
+        host_step()
     a1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = a0.elapsed_time(a1) / args.steps
@@ -507,7 +600,8 @@ def main():
             "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": None,
+            "traffic": TRAFFIC_BYTES.get(args.precision) if ncells == NCELLS else None,
+            "traffic_note": "DRAM bytes per launch (ncu); algorithmic: FP32 tiles in + FP64 Q out = 432 MB",
             "fp64_flops_per_cell": head["fp64_flops_per_cell"],
             "radial_flops_per_cell": head["radial_flops_per_cell"],
             "radial_note": "low-precision radial flops: tensor-core (bf16, tf32) or FP32 CUDA-core (rf32)",
@@ -523,6 +617,7 @@ def main():
             "unit": "cells/s",
             "h2d_bytes_per_step": int(f_pin.numel() * 8),
             "d2h_bytes_per_step": int(q_pin.numel() * 8),
+            "api": f"wef_evaluate_host, pinned host f and Q, chunks of {chunk} cells (copies overlap evaluations)",
         },
         "gpu_launches": 2 * args.steps,
         "clocks": head["clocks"],

@@ -149,6 +149,20 @@ wef_status wef_plan_status(wef_plan plan, int reset);
 wef_status wef_plan_destroy(wef_plan plan);
 
 /*
+ * Evaluation from host memory: the same Q(f, f) for f and Q in host memory (pinned for
+ * the copies to be asynchronous), streamed through the device in chunks of chunk_cells
+ * cells so that the host<->device copies of one chunk overlap the evaluation of another.
+ * The workspace (wef_host_workspace_size(op, chunk_cells, prec), 256-byte aligned, device
+ * memory) holds one chunk's evaluation workspace and two staging slots each for f and Q.
+ * Copies run on two library streams ordered by events; evaluations run on `stream`, which
+ * also waits for the last copy back: q_host is complete once `stream` has.  Calls on one
+ * operator must not overlap.  Errors as wef_evaluate.
+ */
+wef_status wef_host_workspace_size(wef_op op, int64_t chunk_cells, wef_precision prec, int64_t* bytes);
+wef_status wef_evaluate_host(wef_op op, const double* f_host, double* q_host, int64_t ncells, int64_t chunk_cells,
+                             wef_precision prec, void* workspace, int64_t ws_bytes, void* stream);
+
+/*
  * Unfactorised baselines (Sec. 4.5): the same Q(f, f), FP64, without the factorisation,
  * for comparison on the same GPU.  Both use the uploaded (symmetrised, zeroed) core.
  *

@@ -17,7 +17,7 @@ P_loss^c the same with v'_hat -> z_hat, and S_c = sum_m G^2 over the channel
 (the squared norm of the channel's invariant tensor).  The SO(3) integral of
 three Wigner matrices gives 8 pi^2 times the projector onto that invariant.
 
-Readings (the paper is silent or inconsistent):
+Readings (where the paper is silent or inconsistent):
 * collision kernel B = u^gamma / (4 pi)  (isotropic; gamma=0 Maxwell, 1 hard spheres);
 * z = t^2 / 2 with t = (v + w)/sqrt2, so that M(v)M(w) = (2pi)^-3 e^{-z} e^{-z x^2} and the
   generalized Gauss-Laguerre weight z^{gamma/2} e^{-z} of §4.3.3 / Appendix A

@@ -60,6 +60,8 @@ def lib():
             "wef_integrate_workspace_size": ([vp, i64, ctypes.c_int, i64p], ctypes.c_int),
             "wef_integrate": ([vp, vp, i64, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, i64, vp], ctypes.c_int),
             "wef_linearized_apply": ([vp, vp, vp, vp, i64, ctypes.c_int, vp, i64, vp], ctypes.c_int),
+            "wef_host_workspace_size": ([vp, i64, ctypes.c_int, i64p], ctypes.c_int),
+            "wef_evaluate_host": ([vp, vp, vp, i64, i64, ctypes.c_int, vp, i64, vp], ctypes.c_int),
             "wef_naive_evaluate": ([vp, vp, vp, i64, vp, i64, vp], ctypes.c_int),
             "wef_dense_tensor_size": ([vp, i64p], ctypes.c_int),
             "wef_dense_assemble": ([vp, vp, i64, vp], ctypes.c_int),
@@ -204,6 +206,17 @@ def wef_linearized_apply(op, c0_ptr, d_ptr, out_ptr, ncells, prec, ws_ptr, ws_by
     _check(lib().wef_linearized_apply(op, c0_ptr, d_ptr, out_ptr, int(ncells), int(prec), ws_ptr, int(ws_bytes), stream_ptr))
 
 
+def wef_host_workspace_size(op, chunk_cells, prec=WEF_FP64):
+    b = ctypes.c_int64()
+    _check(lib().wef_host_workspace_size(op, int(chunk_cells), int(prec), ctypes.byref(b)))
+    return b.value
+
+
+def wef_evaluate_host(op, f_ptr, q_ptr, ncells, chunk_cells, prec, ws_ptr, ws_bytes, stream_ptr):
+    _check(lib().wef_evaluate_host(op, f_ptr, q_ptr, int(ncells), int(chunk_cells), int(prec), ws_ptr, int(ws_bytes),
+                                   stream_ptr))
+
+
 def wef_naive_evaluate(op, f_ptr, q_ptr, ncells, ws_ptr, ws_bytes, stream_ptr):
     _check(lib().wef_naive_evaluate(op, f_ptr, q_ptr, int(ncells), ws_ptr, int(ws_bytes), stream_ptr))
 
@@ -310,6 +323,26 @@ class Operator:
         wef_linearized_apply(self.h, c0.data_ptr(), d.data_ptr(), out.data_ptr(), d.shape[0], prec, ws.data_ptr(),
                              ws.numel(), st.cuda_stream)
         return out
+
+    def evaluate_host(self, f, q=None, precision="fp64", chunk_cells=4096, stream=None, device=None):
+        """Q(f, f) for f in host memory (a CPU float64 tensor, ideally pinned); the copies of
+        one chunk overlap the evaluation of the next.  Returns q (host) after the stream's
+        work is queued; synchronize the stream before reading it."""
+        import torch
+
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        assert not f.is_cuda and f.dtype == torch.float64 and f.is_contiguous()
+        if q is None:
+            q = torch.empty_like(f, pin_memory=f.is_pinned())
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        need = wef_host_workspace_size(self.h, chunk_cells, prec)
+        ws = getattr(self, "_hws", None)
+        if ws is None or ws.numel() < need or ws.device != dev:
+            self._hws = ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        wef_evaluate_host(self.h, f.data_ptr(), q.data_ptr(), f.shape[0], chunk_cells, prec, ws.data_ptr(), ws.numel(),
+                          st.cuda_stream)
+        return q
 
     def close(self):
         if self.h is not None:

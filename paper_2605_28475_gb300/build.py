@@ -35,8 +35,10 @@ def _compile(cmd):
     return r.stdout + r.stderr
 
 
-def build(verbose=False, extra_nvcc=()):
-    """Compile every translation unit and link libwef.so; returns its path."""
+def build(verbose=False, extra_nvcc=(), defines=()):
+    """Compile every translation unit and link libwef.so; returns its path.
+    `defines` (e.g. ["WEF_RF_J13=4"]) go to both nvcc and g++."""
+    dflags = ["-D" + d for d in defines]
     os.makedirs(OUT_DIR, exist_ok=True)
     cu, cpp = _sources()
     jobs = []
@@ -45,11 +47,11 @@ def build(verbose=False, extra_nvcc=()):
         o = os.path.join(OUT_DIR, f + ".o")
         objs.append(o)
         jobs.append([_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c",
-                     os.path.join(CSRC, f), "-o", o, *extra_nvcc])
+                     os.path.join(CSRC, f), "-o", o, *dflags, *extra_nvcc])
     for f in cpp:
         o = os.path.join(OUT_DIR, f + ".o")
         objs.append(o)
-        jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-c", os.path.join(CSRC, f), "-o", o])
+        jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", *dflags, "-c", os.path.join(CSRC, f), "-o", o])
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         logs = list(ex.map(_compile, jobs))
     if verbose:

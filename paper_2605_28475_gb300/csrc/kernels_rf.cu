@@ -64,6 +64,9 @@ __device__ __forceinline__ double f2d_exact(float x) {
 // program on its own: per channel, per block of J q2 groups, stage 1 for the J groups
 // (core rows as float4, reused by the J groups), then the union of the block's q3: f[:, q3]
 // is loaded once and serves every q2 of the block it pairs with.
+#ifndef WEF_RF_EARLY_ACC
+#define WEF_RF_EARLY_ACC 0
+#endif
 template <int K>
 struct RfCfg {
   static constexpr int KP4 = (K + 3) / 4 * 4;  // padded k2 (float4 core rows)
@@ -80,7 +83,8 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(RfCfg<K>::MAXREG)
     rf_kernel(const float* __restrict__ ftile, double* __restrict__ qout, int64_t ncells, int64_t ntiles, int NQ,
               const int4* __restrict__ tasks, const int4* __restrict__ chans, const int4* __restrict__ blocks,
               const int4* __restrict__ uents, const int4* __restrict__ pairs, const double2* __restrict__ pw,
-              const int32_t* __restrict__ order, int ntasks, const float* __restrict__ R32, int* __restrict__ queue) {
+              const int32_t* __restrict__ order, int ntasks, const float* __restrict__ R32, int* __restrict__ queue,
+              int64_t group) {
   using Cfg = RfCfg<K>;
   constexpr int J = Cfg::J, KP4 = Cfg::KP4, R4 = KP4 / 4, S = K * 32;
   extern __shared__ double qacc[];  // [m1][k1][32]
@@ -93,8 +97,20 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(RfCfg<K>::MAXREG)
     const int64_t it = item_s;
     __syncthreads();
     if (it >= nitems) break;
-    const int task = order[it / ntiles];
-    const int64_t tile = it % ntiles;
+    // Items run tile group by tile group (a group's FP32 tiles stay in L2 while all its
+    // shells pass over them), largest shells first inside a group.
+    const int64_t nfull = ntiles / group, full_items = nfull * group * ntasks;
+    int task;
+    int64_t tile;
+    if (it < full_items) {
+      const int64_t g = it / (group * ntasks), r = it - g * group * ntasks;
+      task = order[r / group];
+      tile = g * group + r % group;
+    } else {
+      const int64_t rem = ntiles - nfull * group, r = it - full_items;
+      task = order[r / rem];
+      tile = nfull * group + r % rem;
+    }
     const int4 T = __ldg(tasks + task);  // q1_base, n1, chan_start, nchan
     const float* ft = ftile + tile * (int64_t)NQ * K * 32 + lane;
     double* acc = qacc + k1 * 32 + lane;
@@ -146,6 +162,14 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(RfCfg<K>::MAXREG)
 #pragma unroll
           for (int j = 0; j < J; ++j) {
             if (!((U.y >> j) & 1)) continue;
+#if WEF_RF_EARLY_ACC
+            // record and accumulators first: their latency overlaps the dot product
+            const int4 P = __ldg(pairs + p);  // ne, q1a offset, q1b offset
+            const double2 W = __ldg(pw + p);
+            ++p;
+            const double a0 = acc[P.y * S];
+            const double a1 = P.x > 1 ? acc[P.z * S] : 0.0;
+#endif
             float b0 = 0.0f, b1 = 0.0f;
 #pragma unroll
             for (int k3 = 0; k3 < K; ++k3) {
@@ -154,11 +178,16 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(RfCfg<K>::MAXREG)
               else b0 = fmaf(A[j][k3], xv, b0);
             }
             const double Bv = f2d_exact(b0 + b1);
+#if WEF_RF_EARLY_ACC
+            acc[P.y * S] = fma(W.x, Bv, a0);
+            if (P.x > 1) acc[P.z * S] = fma(W.y, Bv, a1);
+#else
             const int4 P = __ldg(pairs + p);  // ne, q1a offset, q1b offset
             const double2 W = __ldg(pw + p);
             ++p;
             acc[P.y * S] = fma(W.x, Bv, acc[P.y * S]);
             if (P.x > 1) acc[P.z * S] = fma(W.y, Bv, acc[P.z * S]);
+#endif
           }
         }
       }
@@ -200,8 +229,13 @@ cudaError_t launch_rf_k(const double* f, float* ftile32, int* queue, double* q, 
   int64_t grid = (int64_t)nsm * per_sm;
   if (grid > nitems) grid = nitems;
   if (ev0) cudaEventRecord(ev0, s);
+  // tile groups of ~48 MB of FP32 tiles (well inside the 126 MB L2)
+  const int64_t tile_bytes = (int64_t)NQ * K * 32 * sizeof(float);
+  int64_t group = (48LL << 20) / tile_bytes;
+  if (group < 1) group = 1;
+  if (group > ntiles) group = ntiles;
   rf_kernel<K><<<(unsigned)grid, threads, smem, s>>>(ftile32, q, ncells, ntiles, NQ, r.tasks, r.chans, r.blocks,
-                                                     r.uents, r.pairs, r.pw, r.order, r.ntasks, R32, queue);
+                                                     r.uents, r.pairs, r.pw, r.order, r.ntasks, R32, queue, group);
   if (ev1) cudaEventRecord(ev1, s);
   return cudaGetLastError();
 }

@@ -40,6 +40,10 @@ struct wef_operator {
   int32_t* b_off = nullptr;
   int64_t b_nent = 0;
   void* cublas = nullptr;
+  // evaluation from host memory: copy streams and events, created on first use
+  bool io_ready = false;
+  cudaStream_t io_stream[2] = {nullptr, nullptr};
+  cudaEvent_t io_ev[7] = {};
 
   void release_baselines() {
     cudaFree(b_ent);
@@ -79,6 +83,11 @@ struct wef_operator {
     cudaFree(r_pw);
     r_pw = nullptr;
     release_baselines();
+    if (io_ready) {
+      for (cudaStream_t& s : io_stream) cudaStreamDestroy(s);
+      for (cudaEvent_t& e : io_ev) cudaEventDestroy(e);
+      io_ready = false;
+    }
     release_core();
   }
 };

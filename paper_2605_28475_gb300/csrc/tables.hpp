@@ -47,7 +47,10 @@ struct Program {
 #endif
 
 // q2 groups the radial-first kernel keeps in registers at once (its register budget).
-WEF_HD constexpr int rf_group_width(int K) { return K <= 9 ? 4 : (K <= 13 ? 2 : 1); }
+#ifndef WEF_RF_J13
+#define WEF_RF_J13 2  // for 10 <= K <= 13
+#endif
+WEF_HD constexpr int rf_group_width(int K) { return K <= 9 ? 4 : (K <= 13 ? WEF_RF_J13 : 1); }
 
 // Radial-first program (paper Sec. 4.5.3 ordering with a dense two-stage radial
 // contraction).  One task per output shell l1:

@@ -3,7 +3,8 @@
 Requests (a batch of cells of one (Kmax, Lmax) operator) arrive over time and wait in
 a FIFO.  Whenever one of the stream slots is free, the scheduler takes the shape of
 the oldest waiting request and packs every waiting request of that shape (in arrival
-order, up to a cell cap and what the device arena can hold) into one batch: their
+order, up to a cell cap, an estimated GPU time per batch and what the device arena can
+hold) into one batch: their
 coefficients are copied into one contiguous arena region (device-resident from then
 on) and evaluated by a single wef_evaluate call on the slot's stream.  Requests that
 arrive while batches are on the GPU join the next batch of their shape, and batches
@@ -79,11 +80,31 @@ def _n_per_cell(shape):
     return (km + 1) * (lm + 1) ** 2
 
 
+def pack_batch(waiting, max_cells, cost_per_cell=None, max_batch_s=None):
+    """Requests of the oldest waiting request's shape, in arrival order, while the batch
+    stays within `max_cells` cells and (if costs are given) `max_batch_s` seconds of
+    estimated GPU time.  The oldest request is always taken, whatever its size."""
+    if not waiting:
+        return []
+    shape = waiting[0].shape
+    c = None if cost_per_cell is None else cost_per_cell.get(shape)
+    chosen, cells = [], 0
+    for r in waiting:
+        if r.shape != shape:
+            continue
+        n = r.f.shape[0]
+        if chosen and (cells + n > max_cells or (c is not None and max_batch_s is not None and (cells + n) * c > max_batch_s)):
+            break
+        chosen.append(r)
+        cells += n
+    return chosen
+
+
 class Server:
     """ops: {(kmax, lmax): Operator with an uploaded core}."""
 
     def __init__(self, ops, arena_bytes, nslots=8, precision="tf32", device="cuda:0", max_batch_cells=16384,
-                 keep_results=False):
+                 keep_results=False, cost_per_cell=None, max_batch_s=None):
         import torch
 
         self.torch = torch
@@ -94,6 +115,8 @@ class Server:
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(nslots)]
         self.slot_busy = [None] * nslots  # (requests, event, allocations, q offset)
         self.max_batch_cells = int(max_batch_cells)
+        self.cost_per_cell = cost_per_cell  # {shape: estimated seconds per cell}
+        self.max_batch_s = max_batch_s
         self.keep = keep_results
         self.completed = []
         self.rejected = []
@@ -126,15 +149,8 @@ class Server:
         if slot is None or not waiting:
             return False
         shape = waiting[0].shape
-        chosen, cells = [], 0
-        for r in waiting:
-            if r.shape != shape:
-                continue
-            n = r.f.shape[0]
-            if chosen and cells + n > self.max_batch_cells:
-                break
-            chosen.append(r)
-            cells += n
+        chosen = pack_batch(waiting, self.max_batch_cells, self.cost_per_cell, self.max_batch_s)
+        cells = sum(r.f.shape[0] for r in chosen)
         allocs = self._alloc(self._bytes(shape, cells))
         while allocs is None and len(chosen) > 1:  # shrink the batch to what memory allows
             cells -= chosen.pop().f.shape[0]

@@ -223,3 +223,24 @@ def test_radial_first_full_size_sampled():
     err = _rel(Q[idx], _oracle(km, lm, R, f[idx]))
     print(f"rf32 full-size normwise err {err:.3e}")
     assert err <= RF_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("rf32", RF_TOL), ("tf32", MIXED_TOL["tf32"])])
+def test_maximum_size_sampled_rows(prec, tol):
+    """The largest operator the ABI accepts (Kmax = 16, Lmax = 20, N = 7497 per cell): every
+    path against the oracle on sampled output rows (the invariant rows, the last one and a
+    seeded sample), two cells plus a ragged third."""
+    km, lm, ncells = 16, 20, 3
+    R = wi.random_core(len(gaunt.channels(lm)), km, seed=29)
+    f = wi.random_cells(km, lm, ncells, seed=30)
+    op = W.Operator(km, lm, 1.0)
+    op.upload_core(R)
+    Q = _gpu_eval(op, f, prec).reshape(ncells, -1)
+    N = op.N
+    rows = sorted(set([0, 1, 2, 3, op.NQ, N - 1] + list(np.random.default_rng(1).choice(N, 10, replace=False))))
+    o = dense.DenseOperator(km, lm, dense.conservation_zeroing(R, lm))
+    Qo = o.evaluate_rows(f.reshape(ncells, -1), rows)
+    err = _rel(Q[:, rows], Qo)
+    print(f"{prec} K=17 L=20 sampled-row normwise err {err:.3e}")
+    assert err <= tol
+    assert np.all(Q[:, [0, 1, 2, 3, op.NQ]] == 0.0)

@@ -34,3 +34,17 @@ def test_poisson_requests_seeded():
     assert all(1 <= r.f.shape[0] <= 4096 for r in r1)
     assert all(0 <= r.arrival < 2.0 for r in r1)
     assert sorted(r1) == r1
+
+
+def test_pack_batch_caps():
+    mk = lambda n, sh=(8, 8), t=0.0: serve.Request(t, 0, sh, np.zeros((n, 1)))  # noqa: E731
+    w = [mk(100), mk(50, (12, 12)), mk(300), mk(200), mk(10)]
+    # oldest shape only, in arrival order, up to the cell cap
+    assert [r.f.shape[0] for r in serve.pack_batch(w, 450)] == [100, 300]
+    assert [r.f.shape[0] for r in serve.pack_batch(w, 10_000)] == [100, 300, 200, 10]
+    # estimated-time cap: 1 ms per cell, 0.35 s per batch
+    cost = {(8, 8): 1e-3, (12, 12): 5e-3}
+    assert [r.f.shape[0] for r in serve.pack_batch(w, 10_000, cost, 0.35)] == [100]
+    # the oldest request goes alone even if it exceeds both caps
+    assert [r.f.shape[0] for r in serve.pack_batch([mk(5000)] + w, 450, cost, 0.35)] == [5000]
+    assert serve.pack_batch([], 450) == []
