@@ -40,8 +40,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel at the default workload
 # (K=L=12, 16384 cells), from a one-pass ncu capture of `bench.py --steps 1 --warmup 1
-# --precision rf32` (dram__bytes_read.sum 411.99 MB + dram__bytes_write.sum 328.73 MB).
-TRAFFIC_BYTES = {"rf32": 740.72e6}
+# --precision rf32` (dram__bytes_read.sum 397.91 MB + dram__bytes_write.sum 326.00 MB).
+TRAFFIC_BYTES = {"rf32": 723.91e6}
 
 
 def parse():

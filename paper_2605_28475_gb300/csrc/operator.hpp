@@ -24,7 +24,7 @@ struct wef_operator {
   } dp[2];
   int* d_status = nullptr;  // set by kernels whose bounded waits gave up
   // radial-first program
-  int32_t *r_tasks = nullptr, *r_chans = nullptr, *r_blocks = nullptr, *r_uents = nullptr, *r_pairs = nullptr, *r_order = nullptr;
+  int32_t *r_tasks = nullptr, *r_chans = nullptr, *r_blocks = nullptr, *r_uents = nullptr, *r_order = nullptr;
   double* r_pw = nullptr;
   // core
   double* d_R64 = nullptr;      // symmetrised core [sc][k3][k1][k2]
@@ -76,7 +76,7 @@ struct wef_operator {
     }
     cudaFree(d_status);
     d_status = nullptr;
-    for (int32_t** pp : {&r_tasks, &r_chans, &r_blocks, &r_uents, &r_pairs, &r_order}) {
+    for (int32_t** pp : {&r_tasks, &r_chans, &r_blocks, &r_uents, &r_order}) {
       cudaFree(*pp);
       *pp = nullptr;
     }

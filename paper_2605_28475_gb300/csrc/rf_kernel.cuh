@@ -1,0 +1,290 @@
+// Radial-first contraction kernel, shared by the two translation units that instantiate
+// it with the FP64 accumulators in shared memory or in tensor memory (see kernels_rf.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "wef_internal.hpp"
+
+namespace wef {
+namespace rfk {
+
+// Exact FP32 -> FP64 with 32-bit integer instructions (keeps the FP64 pipe free).
+// FP32 subnormals flush to zero (below 1.2e-38).
+__device__ __forceinline__ double f2d_exact(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  uint32_t hi, lo;
+  if (e == 0u) {
+    hi = sign;
+    lo = 0u;
+  } else if (e == 0xFFu) {
+    hi = sign | 0x7FF00000u | (m >> 3);
+    lo = m << 29;
+  } else {
+    hi = sign | ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Thread mapping: lane = cell, warp = radial row k1 (K warps per CTA).  Each warp walks the
+// program on its own: per channel, per block of J q2 groups, stage 1 for the J groups
+// (core rows as float4, reused by the J groups), then the union of the block's q3: f[:, q3]
+// is loaded once and serves every q2 of the block it pairs with.
+// The shell's FP64 accumulators Q[k1 = warp][q1 offset m][cell = lane].
+// In shared memory: [m][k1][32] doubles.
+struct AccSmem {
+  double* p;  // this thread's slot for m = 0
+  static constexpr bool kTmem = false;
+  __device__ __forceinline__ void zero(int n1, int S) const {
+    for (int m = 0; m < n1; ++m) p[m * S] = 0.0;
+  }
+  __device__ __forceinline__ void add(int m, int S, double w, double b) const { p[m * S] = fma(w, b, p[m * S]); }
+  __device__ __forceinline__ void add2(int ma, int mb, int S, double wa, double wb, double b) const {
+    p[ma * S] = fma(wa, b, p[ma * S]);
+    p[mb * S] = fma(wb, b, p[mb * S]);
+  }
+  __device__ __forceinline__ double get(int m, int S) const { return p[m * S]; }
+};
+
+// In tensor memory: lane = cell within the warp's lane quadrant (warp % 4), two 32-bit
+// columns per value; the warps of one quadrant use disjoint column ranges.  Accesses are
+// warp-uniform (the program is), each read-modify-write waits for its load and store.
+struct AccTmem {
+  uint32_t base;  // TMEM address of m = 0 for this warp
+  static constexpr bool kTmem = true;
+  __device__ __forceinline__ void st(int m, double v) const {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(base + 2u * m),
+                 "r"(__double2loint(v)), "r"(__double2hiint(v))
+                 : "memory");
+  }
+  __device__ __forceinline__ double ld(int m) const {
+    int lo, hi;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(base + 2u * m) : "memory");
+    return __hiloint2double(hi, lo);
+  }
+  __device__ __forceinline__ static void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+  __device__ __forceinline__ static void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+  __device__ __forceinline__ void zero(int n1, int) const {
+    for (int m = 0; m < n1; ++m) st(m, 0.0);
+    wait_st();
+  }
+  __device__ __forceinline__ void add(int m, int, double w, double b) const {
+    double a = ld(m);
+    wait_ld();
+    st(m, fma(w, b, a));
+    wait_st();
+  }
+  __device__ __forceinline__ void add2(int ma, int mb, int, double wa, double wb, double b) const {
+    double a = ld(ma), c = ld(mb);
+    wait_ld();
+    st(ma, fma(wa, b, a));
+    st(mb, fma(wb, b, c));
+    wait_st();
+  }
+  __device__ __forceinline__ double get(int m, int) const {
+    double a = ld(m);
+    wait_ld();
+    return a;
+  }
+};
+template <int K>
+struct RfCfg {
+  static constexpr int KP4 = (K + 3) / 4 * 4;  // padded k2 (float4 core rows)
+  static constexpr int J = rf_group_width(K);   // q2 groups per block (register budget)
+  // Registers per thread that let two CTAs share an SM: each of the 4 sub-partitions has
+  // 16384 registers and takes ceil(2 K / 4) of the two CTAs' warps.
+  static constexpr int WARPS_PER_SMSP = (2 * K + 3) / 4;
+  static constexpr int MAXREG_RAW = 16384 / (32 * WARPS_PER_SMSP) / 8 * 8;
+  static constexpr int MAXREG = MAXREG_RAW > 255 ? 255 : MAXREG_RAW;
+};
+
+template <int K, bool TMEM>
+__global__ void __launch_bounds__(32 * K) __maxnreg__(RfCfg<K>::MAXREG)
+    rf_kernel(const float* __restrict__ ftile, double* __restrict__ qout, int64_t ncells, int64_t ntiles, int NQ,
+              const int4* __restrict__ tasks, const int4* __restrict__ chans, const int4* __restrict__ blocks,
+              const int4* __restrict__ uents, const double2* __restrict__ pw,
+              const int32_t* __restrict__ order, int ntasks, const float* __restrict__ R32, int* __restrict__ queue,
+              int64_t group, int n1max, uint32_t tcols) {
+  using Cfg = RfCfg<K>;
+  constexpr int J = Cfg::J, KP4 = Cfg::KP4, R4 = KP4 / 4, S = K * 32;
+  __shared__ int item_s;
+  const int k1 = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nitems = ntiles * ntasks;
+  // Accumulators in tensor memory: warp k1 uses lane quadrant k1 % 4 and columns from
+  // (k1 / 4) * 2 * n1max on; one allocation for the CTA's lifetime.  Otherwise in
+  // shared memory.
+  __shared__ uint32_t tbase_s;
+  if constexpr (TMEM) {
+    if (k1 == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(&tbase_s)),
+                   "r"(tcols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  extern __shared__ double qacc[];  // [m1][k1][32] (shared-memory accumulators)
+  using Acc = typename std::conditional<TMEM, AccTmem, AccSmem>::type;
+  Acc acc;
+  if constexpr (TMEM)
+    acc = Acc{tbase_s + (((uint32_t)(k1 & 3) * 32u) << 16) + (uint32_t)(k1 >> 2) * 2u * (uint32_t)n1max};
+  else
+    acc = Acc{qacc + k1 * 32 + lane};
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(queue, 1);
+    __syncthreads();
+    const int64_t it = item_s;
+    __syncthreads();
+    if (it >= nitems) break;
+    // Items run tile group by tile group (a group's FP32 tiles stay in L2 while all its
+    // shells pass over them), largest shells first inside a group.
+    const int64_t nfull = ntiles / group, full_items = nfull * group * ntasks;
+    int task;
+    int64_t tile;
+    if (it < full_items) {
+      const int64_t g = it / (group * ntasks), r = it - g * group * ntasks;
+      task = order[r / group];
+      tile = g * group + r % group;
+    } else {
+      const int64_t rem = ntiles - nfull * group, r = it - full_items;
+      task = order[r / rem];
+      tile = nfull * group + r % rem;
+    }
+    const int4 T = __ldg(tasks + task);  // q1_base, n1, chan_start, nchan
+    const float* ft = ftile + tile * (int64_t)NQ * K * 32 + lane;
+    acc.zero(T.y, S);
+    for (int ch = T.z; ch < T.z + T.w; ++ch) {
+      const int4 C = __ldg(chans + ch);  // sc, blk_start, nblk
+      const float4* Ra = reinterpret_cast<const float4*>(R32 + ((int64_t)C.x * K + k1) * K * KP4);  // [k3][k2]
+      for (int b = C.y; b < C.y + C.z; ++b) {
+        const int4 B0 = __ldg(blocks + 2 * b), B1 = __ldg(blocks + 2 * b + 1);  // {nj, u_start, nu}, q2s
+        const int nj = B0.x;
+        const int q2v[4] = {B1.x, B1.y, B1.z, B1.w};
+        float fq[J][KP4];
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+          for (int k2 = 0; k2 < KP4; ++k2) fq[j][k2] = (j < nj && k2 < K) ? __ldg(ft + (q2v[j] * K + k2) * 32) : 0.0f;
+        // stage 1: A[j][k3] = sum_k2 Rt[k1][k2][k3] f[k2][q2_j]
+        float A[J][K];
+#pragma unroll
+        for (int k3 = 0; k3 < K; ++k3) {
+          float a[J];
+#pragma unroll
+          for (int j = 0; j < J; ++j) a[j] = 0.0f;
+#pragma unroll
+          for (int c = 0; c < R4; ++c) {
+            const float4 r = __ldg(Ra + k3 * R4 + c);
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+              a[j] = fmaf(r.x, fq[j][4 * c], a[j]);
+              a[j] = fmaf(r.y, fq[j][4 * c + 1], a[j]);
+              a[j] = fmaf(r.z, fq[j][4 * c + 2], a[j]);
+              a[j] = fmaf(r.w, fq[j][4 * c + 3], a[j]);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < J; ++j) A[j][k3] = a[j];
+        }
+        // stage 2 + FP64 reduction over the union of the block's q3
+        for (int u = B0.y; u < B0.y + B0.z; ++u) {
+          const int4 U = __ldg(uents + u);  // q3 | mask << 16, pair_start, packed targets
+          const int q3 = U.x & 0xFFFF, mask = U.x >> 16;
+          const float* f3 = ft + q3 * K * 32;
+          // J = 1 (large K, tight registers): consume f[:, q3] as it arrives
+          float x[J > 1 ? K : 1];
+          if constexpr (J > 1) {
+#pragma unroll
+            for (int k3 = 0; k3 < K; ++k3) x[k3] = __ldg(f3 + k3 * 32);
+          }
+          int p = U.y;
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            if (!((mask >> j) & 1)) continue;
+            float b0 = 0.0f, b1 = 0.0f;
+#pragma unroll
+            for (int k3 = 0; k3 < K; ++k3) {
+              const float xv = J > 1 ? x[J > 1 ? k3 : 0] : __ldg(f3 + k3 * 32);
+              if (k3 & 1) b1 = fmaf(A[j][k3], xv, b1);
+              else b0 = fmaf(A[j][k3], xv, b0);
+            }
+            const double Bv = f2d_exact(b0 + b1);
+            const uint32_t T = ((uint32_t)(j < 2 ? U.z : U.w) >> (16 * (j & 1))) & 0xFFFFu;  // targets
+            const double2 W = __ldg(pw + p);
+            ++p;
+            if (T & 0x8000u)
+              acc.add2((int)(T & 0xFFu), (int)((T >> 8) & 0x7Fu), S, W.x, W.y, Bv);
+            else
+              acc.add((int)(T & 0xFFu), S, W.x, Bv);
+          }
+        }
+      }
+    }
+    const int64_t cell = tile * 32 + lane;
+    double* qc = qout + cell * (int64_t)K * NQ + (int64_t)k1 * NQ + T.x;
+    for (int m = 0; m < T.y; ++m) {
+      const int q1 = T.x + m;
+      const double v = acc.get(m, S);  // all lanes (tensor-memory loads are warp-wide)
+      // conservation projection: (k1 = 0, q1 = 0..3) and (k1 = 1, q1 = 0) are zero
+      if (cell < ncells) qc[m] = ((k1 == 0 && q1 < 4) || (k1 == 1 && q1 == 0)) ? 0.0 : v;
+    }
+    __syncthreads();
+  }
+  if constexpr (TMEM) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (k1 == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase_s), "r"(tcols) : "memory");
+  }
+}
+
+// Launches the persistent radial-first kernel (the queue was reset and the FP32 tiles
+// written by the caller).
+template <int K, bool TMEM>
+cudaError_t launch_rf_k(const float* ftile32, int* queue, double* q, int64_t ncells, int NQ, const DevRadial& r,
+                        const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+  constexpr int threads = 32 * K;
+  const int64_t ntiles = (ncells + 31) / 32;
+  const size_t smem = TMEM ? 0 : (size_t)r.n1max * threads * sizeof(double);
+  uint32_t tcols = 0;
+  if (TMEM) {
+    // columns: ceil(K / 4) warps share a lane quadrant, 2 columns per FP64 accumulator
+    const uint32_t need = (uint32_t)((K + 3) / 4) * 2u * (uint32_t)r.n1max;
+    tcols = 32;
+    while (tcols < need) tcols <<= 1;
+    if (tcols > 512) return cudaErrorInvalidValue;
+  }
+  static size_t attr = 0;  // dynamic shared memory opted in so far for this instantiation
+  if (smem > attr) {
+    cudaError_t e = cudaFuncSetAttribute(rf_kernel<K, TMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rf_kernel<K, TMEM>, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  if (tcols > 0 && per_sm > (int)(512 / tcols)) per_sm = (int)(512 / tcols);  // tensor memory per SM
+  const int64_t nitems = ntiles * r.ntasks;
+  int64_t grid = (int64_t)nsm * per_sm;
+  if (grid > nitems) grid = nitems;
+  if (ev0) cudaEventRecord(ev0, s);
+  // tile groups of ~48 MB of FP32 tiles (well inside the 126 MB L2)
+  const int64_t tile_bytes = (int64_t)NQ * K * 32 * sizeof(float);
+  int64_t group = (48LL << 20) / tile_bytes;
+  if (group < 1) group = 1;
+  if (group > ntiles) group = ntiles;
+  rf_kernel<K, TMEM><<<(unsigned)grid, threads, smem, s>>>(ftile32, q, ncells, ntiles, NQ, r.tasks, r.chans, r.blocks,
+                                                     r.uents, r.pw, r.order, r.ntasks, R32, queue, group,
+                                                     r.n1max, tcols);
+  if (ev1) cudaEventRecord(ev1, s);
+  return cudaGetLastError();
+}
+
+}  // namespace rfk
+}  // namespace wef

@@ -299,12 +299,15 @@ std::string build_tables(int kmax, int lmax, Tables& t) {
           for (int j = 0; j < 4; ++j) RP.blocks.push_back(j < nj ? q2s[b0 + j] : 0);
           for (const auto& mk : mask) {
             const int q3 = mk.first;
-            RP.uents.insert(RP.uents.end(), {q3, mk.second, (int32_t)(RP.pairs.size() / 4), 0});
+            const size_t u = RP.uents.size();
+            RP.uents.insert(RP.uents.end(), {q3 | mk.second << 16, (int32_t)(RP.pw.size() / 2), 0, 0});
             for (int j = 0; j < nj; ++j) {
               if (!(mk.second >> j & 1)) continue;
               const auto& v = byp[q2s[b0 + j]][q3];
               if (v.size() > 2) return "a radial-first pair feeding more than two q1";
-              RP.pairs.insert(RP.pairs.end(), {(int32_t)v.size(), v[0].first, v.size() > 1 ? v[1].first : v[0].first, 0});
+              if (n1 > 127) return "a shell too large for the radial-first target encoding";
+              const int32_t T = v[0].first | (v.size() > 1 ? v[1].first : 0) << 8 | (v.size() > 1 ? 1 << 15 : 0);
+              RP.uents[u + 2 + j / 2] = (int32_t)((uint32_t)RP.uents[u + 2 + j / 2] | (uint32_t)T << (16 * (j & 1)));
               RP.pw.push_back(v[0].second);
               RP.pw.push_back(v.size() > 1 ? v[1].second : 0.0);
               cost += 2.0 * K * K + 2.0 * K * (double)v.size();

@@ -59,15 +59,17 @@ WEF_HD constexpr int rf_group_width(int K) { return K <= 9 ? 4 : (K <= 13 ? WEF_
 //   blocks: two int4 per block: {nj, u_start, nu, 0}, {q2_0, q2_1, q2_2, q2_3}: up to
 //           J = rf_group_width(K) of the channel's q2 (the smaller shell), whose stage-1
 //           products A(q2_j) are held together
-//   uents:  {q3, mask, pair_start, 0}: each q3 paired with any q2 of the block, once; bit j
-//           of mask set if (q2_j, q3) is a pair; its pairs follow in j order
-//   pairs:  {ne, q1a - q1_base, q1b - q1_base, 0}, weights pw {ga, gb} (gb = 0 if ne = 1)
+//   uents:  {q3 | mask << 16, pair_start, T_0 | T_1 << 16, T_2 | T_3 << 16}: each q3 paired
+//           with any q2 of the block, once; bit j of mask set if (q2_j, q3) is a pair, whose
+//           targets are T_j = (q1a - q1_base) | (q1b - q1_base) << 8 | (ne == 2) << 15 and
+//           whose weights pw[pair] = {ga, gb} (gb = 0 if ne = 1) follow from pair_start in
+//           j order
 // order:  task indices by decreasing cost (the persistent kernel's schedule).
 // Grouping by q2 makes stage 1 (2K^3 flops per q2 group) run over 4067 instead of 6125
 // groups at K = L = 12; walking the union of the block's q3 loads each f[:, q3] once per
 // block instead of once per pair (32707 instead of 56981 loads of K values for J = 2).
 struct RadialProgram {
-  std::vector<int32_t> tasks, chans, blocks, uents, pairs;
+  std::vector<int32_t> tasks, chans, blocks, uents;
   std::vector<double> pw;
   std::vector<int32_t> order;
   std::vector<double> task_cost;  // FP64 + FP32 flops per cell, for the schedule

@@ -75,7 +75,6 @@ cudaError_t ensure_device(wef_operator* op) {
   if (e == cudaSuccess) e = upload(&op->r_chans, RP.chans);
   if (e == cudaSuccess) e = upload(&op->r_blocks, RP.blocks);
   if (e == cudaSuccess) e = upload(&op->r_uents, RP.uents);
-  if (e == cudaSuccess) e = upload(&op->r_pairs, RP.pairs);
   if (e == cudaSuccess) e = upload(&op->r_pw, RP.pw);
   if (e == cudaSuccess) e = upload(&op->r_order, RP.order);
   if (e == cudaSuccess) e = cudaMalloc((void**)&op->d_status, sizeof(int));
@@ -233,7 +232,7 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
   if (prec == WEF_RADIAL_FP32) {
     const RadialProgram& RP = op->T.rprog;
     DevRadial r{(const int4*)op->r_tasks, (const int4*)op->r_chans, (const int4*)op->r_blocks,
-                (const int4*)op->r_uents, (const int4*)op->r_pairs, (const double2*)op->r_pw, op->r_order,
+                (const int4*)op->r_uents, (const double2*)op->r_pw, op->r_order,
                 (int)RP.task_cost.size(), RP.n1max};
     cudaError_t er = launch_rf(K, f_dev, (float*)((char*)workspace + 256), (int*)workspace, q_dev, ncells, NQ, r,
                                op->d_R32, op->sms, s, op->trace_start, op->trace_stop);

@@ -27,7 +27,6 @@ struct DevRadial {
   const int4* chans = nullptr;
   const int4* blocks = nullptr;
   const int4* uents = nullptr;
-  const int4* pairs = nullptr;
   const double2* pw = nullptr;
   const int32_t* order = nullptr;
   int ntasks = 0;
