@@ -34,6 +34,11 @@ def test_alone_equals_in_mix(prec):
     reqs = serve.poisson_requests(400.0, 0.15, shapes, 200, seed=9,
                                   make_cells=lambda sh, n, s: wi.random_cells(sh[0], sh[1], n, seed=s))
     assert len(reqs) > 20
+    # a burst at t = 0 is always batched (three requests of each shape wait together);
+    # the Poisson stream then arrives while batches are on the GPU
+    burst = [serve.Request(0.0, 1000 + i, shapes[i % 3], wi.random_cells(*shapes[i % 3], 20, seed=500 + i))
+             for i in range(9)]
+    reqs = sorted(burst + reqs)
     # a small arena forces some requests to wait for memory
     srv = serve.Server(ops, arena_bytes=16 << 20, nslots=3, precision=prec, keep_results=True, max_batch_cells=500)
     res = serve.run(srv, reqs)
