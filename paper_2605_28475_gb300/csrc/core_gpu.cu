@@ -29,12 +29,15 @@ namespace {
 
 constexpr int kMaxL1 = 21;  // Lmax <= 20
 constexpr int kMaxK = 17;   // Kmax <= 16
-constexpr int kNP = 32;     // patch-2 radial points per contraction step
+constexpr int kNP = 64;     // patch-2 radial points per contraction step
 constexpr int kNA = 128;    // patch-1 angular points per piece
 
+// Point tables are component-major (component c of point p at [c * npoints + p]) so that
+// the contraction's reads of one component over consecutive points are coalesced.
 struct Geo {
   int K, L1, nz_chunk, Nx1, Nh1, Ny2, Nh2, nft;
-  int DA, DR;        // doubles per angular / radial point record
+  int DA, DR;        // components per angular / radial point
+  int64_t na, nr;    // angular / radial points in the chunk (the component strides)
   int64_t na_zh;     // angular points per (z, half)
   int64_t nr_zh;     // radial points per (z, half)
   double gamma, pref;
@@ -98,8 +101,8 @@ __device__ __forceinline__ void radial_lane(const Geo& g, const Dev& d, int l, d
   }
 }
 
-// Lane l: cos-type real harmonics Y_{l m}(ct, azimuth 0), m = 0..l, into out[l*L1 + m].
-__device__ __forceinline__ void ylm_lane(const Geo& g, const Dev& d, int l, double ct, double* out) {
+// Lane l: cos-type real harmonics Y_{l m}(ct, azimuth 0), m = 0..l, into out[(l*L1 + m) * stride].
+__device__ __forceinline__ void ylm_lane(const Geo& g, const Dev& d, int l, double ct, double* out, int64_t stride) {
   const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
   double pmm = 1.0;
   for (int m = 0; m <= l; ++m) {
@@ -112,11 +115,11 @@ __device__ __forceinline__ void ylm_lane(const Geo& g, const Dev& d, int l, doub
       pprev = p;
       p = pn;
     }
-    out[l * g.L1 + m] = d.ylm_norm[l * g.L1 + m] * p;
+    out[(l * g.L1 + m) * stride] = d.ylm_norm[l * g.L1 + m] * p;
   }
 }
 
-// Kernel 1a: one warp per angular point of the chunk: record = {W, eps[K][L1], Yv[L1][L1], Yw[L1][L1]}.
+// Kernel 1a: one warp per angular point of the chunk; components {W, eps[K][L1], Yv[L1][L1], Yw[L1][L1]}.
 __global__ void angular_points_kernel(Geo g, Dev d, int iz0, double* __restrict__ A) {
   const int64_t gp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int l = threadIdx.x & 31;
@@ -136,7 +139,8 @@ __global__ void angular_points_kernel(Geo g, Dev d, int iz0, double* __restrict_
     ih = (int)(r % g.Nh2);
   }
   const Pt p = point_geo(g, d, iz, half, patch, io, ih);
-  double* rec = A + gp * g.DA;
+  double* rec = A + gp;  // component c at rec[c * na]
+  const int64_t sa = g.na;
   const double sb = 2.0 * p.y * sqrt(fmax(0.0, 1.0 - p.y * p.y));
   const double Vx = 0.5 * p.w * sb, Vz = 0.5 * (p.v + p.w * p.cb);
   const double Vm = sqrt(Vx * Vx + Vz * Vz);
@@ -163,13 +167,13 @@ __global__ void angular_points_kernel(Geo g, Dev d, int iz0, double* __restrict_
       const double wt = 0.5 * d.ftw[i] * pl;
       for (int k = 0; k < g.K; ++k) eps[k] += wt * Rr[k];
     }
-    for (int k = 0; k < g.K; ++k) rec[1 + k * g.L1 + l] = eps[k];
-    ylm_lane(g, d, l, Vm > 0 ? Vz / Vm : 1.0, rec + 1 + g.K * g.L1);
-    ylm_lane(g, d, l, p.cb, rec + 1 + g.K * g.L1 + g.L1 * g.L1);
+    for (int k = 0; k < g.K; ++k) rec[(1 + k * g.L1 + l) * sa] = eps[k];
+    ylm_lane(g, d, l, Vm > 0 ? Vz / Vm : 1.0, rec + (1 + g.K * g.L1) * sa, sa);
+    ylm_lane(g, d, l, p.cb, rec + (1 + g.K * g.L1 + g.L1 * g.L1) * sa, sa);
   }
 }
 
-// Kernel 1b: one warp per radial point: record = {Rv[K][L1], Rw[K][L1]}.
+// Kernel 1b: one warp per radial point; components {Rv[K][L1], Rw[K][L1]}.
 __global__ void radial_points_kernel(Geo g, Dev d, int iz0, double* __restrict__ Rr) {
   const int64_t rp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int l = threadIdx.x & 31;
@@ -185,11 +189,12 @@ __global__ void radial_points_kernel(Geo g, Dev d, int iz0, double* __restrict__
     p = point_geo(g, d, iz, half, 2, (int)(r / g.Nh2), (int)(r % g.Nh2));
   }
   double out[kMaxK];
-  double* rec = Rr + rp * g.DR;
+  double* rec = Rr + rp;
+  const int64_t sr = g.nr;
   radial_lane(g, d, l, p.v, out);
-  for (int k = 0; k < g.K; ++k) rec[k * g.L1 + l] = out[k];
+  for (int k = 0; k < g.K; ++k) rec[(k * g.L1 + l) * sr] = out[k];
   radial_lane(g, d, l, p.w, out);
-  for (int k = 0; k < g.K; ++k) rec[g.K * g.L1 + k * g.L1 + l] = out[k];
+  for (int k = 0; k < g.K; ++k) rec[(g.K * g.L1 + k * g.L1 + l) * sr] = out[k];
 }
 
 struct ChanDev {
@@ -199,17 +204,18 @@ struct ChanDev {
   const double* fscale;  // 8 pi^2 / S_c
 };
 
-// a_c W and b_c W of one angular point record.
+// a_c W and b_c W of angular point rec (component c at rec[c * na]).
 __device__ __forceinline__ void ab_of(const Geo& g, const Dev& d, const double* rec, int l1, int l3, const double* G,
                                       double& aW, double& bW) {
+  const int64_t sa = g.na;
   const double W = rec[0];
-  const double* Yv = rec + 1 + g.K * g.L1;
-  const double* Yw = Yv + g.L1 * g.L1;
+  const double* Yv = rec + (1 + g.K * g.L1) * sa;
+  const double* Yw = Yv + g.L1 * g.L1 * sa;
   const int mm = l1 < l3 ? l1 : l3;
   double a = 0.0;
-  for (int m = 0; m <= mm; ++m) a += G[m] * Yw[l3 * g.L1 + m] * Yv[l1 * g.L1 + m];
+  for (int m = 0; m <= mm; ++m) a += G[m] * Yw[(l3 * g.L1 + m) * sa] * Yv[(l1 * g.L1 + m) * sa];
   aW = W * a;
-  bW = W * G[0] * Yw[l3 * g.L1] * d.ylm_norm[l1 * g.L1];
+  bW = W * G[0] * Yw[l3 * g.L1 * sa] * d.ylm_norm[l1 * g.L1];
 }
 
 // Kernel 2: one CTA per channel, thread (k1, k2) accumulates R_c[k1][k2][0..K) over the chunk
@@ -230,33 +236,31 @@ __global__ void contract_kernel(Geo g, Dev d, ChanDev cd, const double* __restri
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
-  const int64_t nzh = (int64_t)g.nz_chunk * 2;
+  const int64_t nzh = (int64_t)g.nz_chunk * 2, sa = g.na, sr = g.nr;
   for (int64_t zh = 0; zh < nzh; ++zh) {
-    const double* Az = A + zh * g.na_zh * g.DA;
-    const double* Rz = Rr + zh * g.nr_zh * g.DR;
+    const double* Az = A + zh * g.na_zh;  // point p of this (z, half): Az + p, component c at + c * sa
+    const double* Rz = Rr + zh * g.nr_zh;
     // patch 1: one radial point per outer node, alpha summed over the inner node
     for (int io = 0; io < g.Nx1; ++io) {
-      const double* rrec = Rz + (int64_t)io * g.DR;
+      const double* rrec = Rz + io;
       double al = 0.0;  // thread k < K: alpha[k]
       for (int h0 = 0; h0 < g.Nh1; h0 += kNA) {
         const int nh = min(kNA, g.Nh1 - h0);
         __syncthreads();
         for (int i = t; i < nh; i += blockDim.x)
-          ab_of(g, d, Az + ((int64_t)io * g.Nh1 + h0 + i) * g.DA, l1, l3, G, aW[i], bW[i]);
+          ab_of(g, d, Az + (int64_t)io * g.Nh1 + h0 + i, l1, l3, G, aW[i], bW[i]);
         __syncthreads();
         if (t < K) {
-          const double rv = rrec[t * L1 + l1];
-          for (int i = 0; i < nh; ++i) {
-            const double* rec = Az + ((int64_t)io * g.Nh1 + h0 + i) * g.DA;
-            al += aW[i] * rec[1 + t * L1 + l1] - bW[i] * rv;
-          }
+          const double rv = rrec[(t * L1 + l1) * sr];
+          const double* eps = Az + (int64_t)io * g.Nh1 + h0 + (1 + t * L1 + l1) * sa;
+          for (int i = 0; i < nh; ++i) al += aW[i] * eps[i] - bW[i] * rv;
         }
       }
       __syncthreads();
       if (t < K) {
         alpha[t][0] = s2 * al;
-        rv2[t][0] = rrec[t * L1 + l2];
-        rw3[t][0] = rrec[K * L1 + t * L1 + l3];
+        rv2[t][0] = rrec[(t * L1 + l2) * sr];
+        rw3[t][0] = rrec[(K * L1 + t * L1 + l3) * sr];
       }
       __syncthreads();
       if (own) {
@@ -271,15 +275,15 @@ __global__ void contract_kernel(Geo g, Dev d, ChanDev cd, const double* __restri
       const int np = (int)min((int64_t)kNP, n2 - p0);
       __syncthreads();
       for (int i = t; i < np; i += blockDim.x)
-        ab_of(g, d, Az + ((int64_t)g.Nx1 * g.Nh1 + p0 + i) * g.DA, l1, l3, G, aW[i], bW[i]);
+        ab_of(g, d, Az + (int64_t)g.Nx1 * g.Nh1 + p0 + i, l1, l3, G, aW[i], bW[i]);
       __syncthreads();
       for (int i = t; i < K * np; i += blockDim.x) {
-        const int k = i / np, j = i % np;
-        const double* rec = Az + ((int64_t)g.Nx1 * g.Nh1 + p0 + j) * g.DA;
-        const double* rrec = Rz + ((int64_t)g.Nx1 + p0 + j) * g.DR;
-        alpha[k][j] = s2 * (aW[j] * rec[1 + k * L1 + l1] - bW[j] * rrec[k * L1 + l1]);
-        rv2[k][j] = rrec[k * L1 + l2];
-        rw3[k][j] = rrec[K * L1 + k * L1 + l3];
+        const int k = i / np, j = i % np;  // consecutive threads: consecutive points (coalesced)
+        const double* rec = Az + (int64_t)g.Nx1 * g.Nh1 + p0 + j;
+        const double* rrec = Rz + (int64_t)g.Nx1 + p0 + j;
+        alpha[k][j] = s2 * (aW[j] * rec[(1 + k * L1 + l1) * sa] - bW[j] * rrec[(k * L1 + l1) * sr]);
+        rv2[k][j] = rrec[(k * L1 + l2) * sr];
+        rw3[k][j] = rrec[(K * L1 + k * L1 + l3) * sr];
       }
       __syncthreads();
       if (own) {
@@ -391,6 +395,8 @@ extern "C" wef_status wef_core_build_device(wef_op op, int pad_rad, int pad_ang,
   for (int iz0 = 0; iz0 < Nz && e == cudaSuccess; iz0 += zc) {
     g.nz_chunk = std::min(zc, Nz - iz0);
     const int64_t na = (int64_t)g.nz_chunk * 2 * g.na_zh, nr = (int64_t)g.nz_chunk * 2 * g.nr_zh;
+    g.na = na;
+    g.nr = nr;
     angular_points_kernel<<<(unsigned)((na * 32 + 255) / 256), 256>>>(g, d, iz0, A);
     radial_points_kernel<<<(unsigned)((nr * 32 + 255) / 256), 256>>>(g, d, iz0, Rr);
     e = cudaGetLastError();
