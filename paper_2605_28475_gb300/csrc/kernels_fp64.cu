@@ -96,12 +96,9 @@ cudaError_t launch_fp64_k(const double* ftile, double* q, int64_t ncells, int NQ
                           const int32_t* chunks, int nchunks, const double* R64, cudaStream_t s) {
   const int64_t ntiles = (ncells + 31) / 32;
   const size_t smem = (size_t)K * K * 32 * sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(fp64_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<size_t> attr[kMaxDevices];
+  cudaError_t e = smem_opt_in(fp64_kernel<K>, smem, attr);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)ntiles, (unsigned)nchunks);
   fp64_kernel<K><<<grid, 32 * K, smem, s>>>(ftile, q, ncells, NQ, p.prog, p.groups, p.gw, p.task_off, chunks, R64);
   return cudaGetLastError();

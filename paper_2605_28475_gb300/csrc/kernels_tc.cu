@@ -343,12 +343,9 @@ cudaError_t launch_tc_k(const double* ftile, double* q, int64_t ncells, int NQ, 
   using S = TcShape<K, TF32>;
   static_assert(S::SMEM <= 232448, "shared memory");
   const int64_t ntiles = (ncells + 31) / 32;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_kernel<K, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<size_t> attr[kMaxDevices];
+  cudaError_t e = smem_opt_in(tc_kernel<K, TF32>, (size_t)S::SMEM, attr);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)ntiles, (unsigned)nchunks);
   tc_kernel<K, TF32><<<grid, 32 * tc_warps<K>(), S::SMEM, s>>>(ftile, q, ncells, NQ, p.prog, p.groups, p.gw,
                                                               p.task_off, chunks, Btiles, status);

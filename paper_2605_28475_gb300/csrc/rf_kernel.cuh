@@ -30,15 +30,10 @@ __device__ __forceinline__ double f2d_exact(float x) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// Thread mapping: lane = cell, warp = radial row k1 (K warps per CTA).  Each warp walks the
-// program on its own: per channel, per block of J q2 groups, stage 1 for the J groups
-// (core rows as float4, reused by the J groups), then the union of the block's q3: f[:, q3]
-// is loaded once and serves every q2 of the block it pairs with.
-// The shell's FP64 accumulators Q[k1 = warp][q1 offset m][cell = lane].
-// In shared memory: [m][k1][32] doubles.
+// The shell's FP64 accumulators Q[k1 = warp][q1 offset m][cell = lane], in shared memory
+// as [m][k1][32] doubles.
 struct AccSmem {
   double* p;  // this thread's slot for m = 0
-  static constexpr bool kTmem = false;
   __device__ __forceinline__ void zero(int n1, int S) const {
     for (int m = 0; m < n1; ++m) p[m * S] = 0.0;
   }
@@ -55,7 +50,6 @@ struct AccSmem {
 // warp-uniform (the program is), each read-modify-write waits for its load and store.
 struct AccTmem {
   uint32_t base;  // TMEM address of m = 0 for this warp
-  static constexpr bool kTmem = true;
   __device__ __forceinline__ void st(int m, double v) const {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(base + 2u * m),
                  "r"(__double2loint(v)), "r"(__double2hiint(v))
@@ -91,6 +85,10 @@ struct AccTmem {
     return a;
   }
 };
+// Thread mapping: lane = cell, warp = radial row k1 (K warps per CTA).  Each warp walks the
+// program on its own: per channel, per block of J q2 groups, stage 1 for the J groups
+// (core rows as float4, reused by the J groups), then the union of the block's q3: f[:, q3]
+// is loaded once and serves every q2 of the block it pairs with.
 template <int K>
 struct RfCfg {
   static constexpr int KP4 = (K + 3) / 4 * 4;  // padded k2 (float4 core rows)
@@ -260,11 +258,10 @@ cudaError_t launch_rf_k(const float* ftile32, int* queue, double* q, int64_t nce
     while (tcols < need) tcols <<= 1;
     if (tcols > 512) return cudaErrorInvalidValue;
   }
-  static size_t attr = 0;  // dynamic shared memory opted in so far for this instantiation
-  if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(rf_kernel<K, TMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<size_t> attr[kMaxDevices];  // dynamic shared memory opted in, per device
+  if (smem > 0) {
+    cudaError_t e = smem_opt_in(rf_kernel<K, TMEM>, smem, attr);
     if (e != cudaSuccess) return e;
-    attr = smem;
   }
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rf_kernel<K, TMEM>, threads, smem);

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <complex>
 #include <map>
+#include <set>
 
 namespace wef {
 
@@ -286,8 +287,33 @@ std::string build_tables(int kmax, int lmax, Tables& t) {
         for (int m = 0; m < n1; ++m)
           for (const Entry& e : sl[(size_t)sc * t.NQ + q1b + m]) byp[e.q2][e.q3].push_back({m, e.w});
         if (byp.empty()) continue;
+        // q2 groups ordered so that each block of J shares as many q3 as possible: greedily,
+        // the first remaining group, then the J-1 groups sharing the most q3 with the block.
         std::vector<int> q2s;
-        for (const auto& kv : byp) q2s.push_back(kv.first);
+        {
+          std::vector<int> rest;
+          for (const auto& kv : byp) rest.push_back(kv.first);
+          while (!rest.empty()) {
+            std::set<int> uni;
+            for (const auto& kv : byp[rest.front()]) uni.insert(kv.first);
+            q2s.push_back(rest.front());
+            rest.erase(rest.begin());
+            for (int j = 1; j < J && !rest.empty(); ++j) {
+              size_t best = 0, best_shared = 0;
+              for (size_t i = 0; i < rest.size(); ++i) {
+                size_t shared = 0;
+                for (const auto& kv : byp[rest[i]]) shared += uni.count(kv.first);
+                if (shared > best_shared) {
+                  best_shared = shared;
+                  best = i;
+                }
+              }
+              for (const auto& kv : byp[rest[best]]) uni.insert(kv.first);
+              q2s.push_back(rest[best]);
+              rest.erase(rest.begin() + (long)best);
+            }
+          }
+        }
         const int bs = (int)RP.blocks.size() / 8;
         int nblk = 0;
         for (size_t b0 = 0; b0 < q2s.size(); b0 += J) {

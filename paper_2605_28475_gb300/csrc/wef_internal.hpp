@@ -8,6 +8,8 @@
 #include "tables.hpp"
 #include "../../include/wef.h"
 
+#include <atomic>
+
 namespace wef {
 
 // Device copy of one Program (see tables.hpp).
@@ -32,6 +34,25 @@ struct DevRadial {
   int ntasks = 0;
   int n1max = 1;
 };
+
+// Opts a kernel in to `bytes` of dynamic shared memory on the current device, once per
+// device and size (function attributes are per device).  `done` holds one entry per device.
+constexpr int kMaxDevices = 64;
+template <class Fn>
+cudaError_t smem_opt_in(Fn fn, size_t bytes, std::atomic<size_t>* done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (done[dev].load(std::memory_order_relaxed) >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) {
+    size_t cur = done[dev].load(std::memory_order_relaxed);
+    while (cur < bytes && !done[dev].compare_exchange_weak(cur, bytes)) {
+    }
+  }
+  return e;
+}
 
 // Releases the cuBLAS handle of the dense baseline.
 void destroy_cublas(void* handle);
