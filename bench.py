@@ -40,8 +40,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel at the default workload
 # (K=L=12, 16384 cells), from a one-pass ncu capture of `bench.py --steps 1 --warmup 1
-# --precision rf32` (dram__bytes_read.sum 397.91 MB + dram__bytes_write.sum 326.00 MB).
-TRAFFIC_BYTES = {"rf32": 723.91e6}
+# --precision rf32` (dram__bytes_read.sum 398.05 MB + dram__bytes_write.sum 325.89 MB).
+TRAFFIC_BYTES = {"rf32": 723.94e6}
 
 
 def parse():
@@ -119,6 +119,23 @@ def cpu_baseline(sample_cells, sample_rows, seed=3):
         "sample": f"{sample_cells} cells x {sample_rows} of {N} output rows (dense C slices), {dt:.1f} s; "
         f"numpy BLAS threads default (all {os.cpu_count()} host cores)",
     }
+
+
+def cpu_angular_first(sample_cells=32, seed=3):
+    """The paper's factorised angular-first contraction (Sec. 4.5.4) in plain numpy on the
+    host, timed on `sample_cells` cells: a CPU comparison point for the factorisation."""
+    import wef_inputs as wi
+    from oracle import angular_first, gaunt
+
+    R = wi.random_core(len(gaunt.channels(LMAX)), KMAX, seed=11)
+    f = wi.two_maxwellians(KMAX, LMAX, sample_cells, seed=seed)
+    sl = angular_first.slices(LMAX)
+    t0 = time.perf_counter()
+    angular_first.evaluate(KMAX, LMAX, R, f, sl=sl)
+    dt = time.perf_counter() - t0
+    return {"value": sample_cells / dt, "unit": "cells/s", "cores": os.cpu_count(),
+            "kind": "angular-first numpy (Sec. 4.5.4)",
+            "sample": f"{sample_cells} cells, {dt:.1f} s; numpy threads default"}
 
 
 class ClockSampler:
@@ -624,6 +641,7 @@ def main():
     }
     if world == 1 and os.environ.get("WEF_BENCH_NO_CPU") != "1":
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_cells, args.cpu_sample_rows)
+        line["cpu_angular_first"] = cpu_angular_first()
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -16,6 +16,9 @@ dense   null-space / detailed-balance zeroing and the dense contraction
         Q_a = sum_bc C_abc f_b f_c with C = R * G (§2.3, §4.1, §4.4, §4.5.1)
 core    the reduced kinematic core R by 5D singular quadrature
         (§3.2-3.3, §4.3, Appendix A, Appendix B)
+angular_first
+        the paper's factorised angular-first contraction (§4.5.4) in plain numpy,
+        pinned to dense; a CPU comparison point for the bench
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` against closed forms or values printed in the paper

@@ -105,3 +105,17 @@ def test_bilinear_symmetric_part_only():
     Q1 = dense.DenseOperator(km, lm, R).evaluate(f)
     Q2 = dense.DenseOperator(km, lm, Rs).evaluate(f)
     assert np.allclose(Q1, Q2, atol=1e-13)
+
+
+@pytest.mark.parametrize("km,lm,ncells", [(0, 0, 3), (2, 3, 7), (3, 4, 5)])
+def test_angular_first_equals_dense(km, lm, ncells):
+    """The factorised angular-first evaluation (§4.5.4) and the dense form (§4.5.1) are the
+    same bilinear form: equal to rounding on a random core and random cells."""
+    from oracle import angular_first
+
+    rng = np.random.default_rng(km * 10 + lm)
+    R = rng.standard_normal((len(gaunt.channels(lm)), km + 1, km + 1, km + 1))
+    f = rng.standard_normal((ncells, km + 1, (lm + 1) ** 2))
+    Qa = angular_first.evaluate(km, lm, R, f)
+    Qd = dense.evaluate(km, lm, R, f.reshape(ncells, -1)).reshape(f.shape)
+    assert np.max(np.abs(Qa - Qd)) <= 1e-12 * max(np.max(np.abs(Qd)), 1.0)
