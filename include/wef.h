@@ -206,6 +206,11 @@ wef_status wef_linearized_apply(wef_op op, const double* c0_dev, const double* d
                                 wef_precision prec, void* workspace, int64_t ws_bytes, void* stream);
 
 /*
+ * Devices: an operator lives on the device that was current when its core was first
+ * uploaded; evaluation calls must be made with that device current (WEF_EINVAL otherwise).
+ */
+
+/*
  * wef_core_build - the kinematic core R[c][k1][k2][k3] of the operator by the
  * singular quadrature of Sec. 4.3 / Appendix A-B, on the host (all cores of the
  * machine).  pad_rad / pad_ang are the selective paddings of Appendix B (the

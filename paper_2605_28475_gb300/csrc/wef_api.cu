@@ -227,6 +227,11 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
   wef_workspace_size(op, ncells, prec, &need);
   if (workspace_bytes < need) return fail(WEF_EINVAL, "wef_evaluate: workspace too small");
   if (ncells > (int64_t)65535 * 32 * 1024) return fail(WEF_EINVAL, "wef_evaluate: ncells too large");
+  {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != op->device)
+      return fail(WEF_EINVAL, "wef_evaluate: the current device is not the one the core was uploaded on");
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const int K = op->T.K, NQ = op->T.NQ;
   if (prec == WEF_RADIAL_FP32) {

@@ -48,3 +48,29 @@ def test_host_evaluation_pageable_and_errors():
         W.wef_evaluate_host(op.h, f.data_ptr(), qh.data_ptr(), n, 0, 0, ws.data_ptr(), ws.numel(), st)
     W.wef_evaluate_host(op.h, 0, 0, 0, 16, 0, 0, 0, st)  # empty batch: nothing to do
     assert np.isfinite(qh.numpy()).all()
+
+
+@pytest.mark.parametrize("prec", ["rf32", "fp64", "tf32"])
+def test_evaluation_captured_in_a_cuda_graph(prec):
+    """wef_evaluate launches only stream-ordered work (no allocation, no synchronisation), so
+    a caller can capture it in a CUDA graph: replays give the direct call's Q bit for bit."""
+    km, lm, n = 4, 5, 70
+    op = W.Operator(km, lm, 1.0)
+    op.upload_core(wi.random_core(len(gaunt.channels(lm)), km, seed=31))
+    f = torch.from_numpy(wi.random_cells(km, lm, n, seed=32)).cuda()
+    q_direct = op.evaluate(f, precision=prec).clone()
+    q = torch.empty_like(f)
+    p = W.PRECISIONS[prec]
+    ws = torch.empty(W.wef_workspace_size(op.h, n, p), dtype=torch.uint8, device="cuda")
+    W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), n, p, ws.data_ptr(), ws.numel(),
+                   torch.cuda.current_stream().cuda_stream)  # first call outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), n, p, ws.data_ptr(), ws.numel(),
+                       torch.cuda.current_stream().cuda_stream)
+    q.zero_()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(q, q_direct)
