@@ -218,14 +218,15 @@ __device__ __forceinline__ void ab_of(const Geo& g, const Dev& d, const double* 
   bW = W * G[0] * Yw[l3 * g.L1 * sa] * d.ylm_norm[l1 * g.L1];
 }
 
-// Kernel 2: one CTA per channel, thread (k1, k2) accumulates R_c[k1][k2][0..K) over the chunk
-// (K is a template parameter so that the K accumulators stay in registers).
+// Kernel 2: S CTAs per channel, each over every S-th radial point of the chunk; thread
+// (k1, k2) accumulates R_c[k1][k2][0..K) in registers (K is a template parameter) and adds
+// its share to R atomically at the end (S is chosen so that the grid fills several waves).
 template <int K>
 __global__ void contract_kernel(Geo g, Dev d, ChanDev cd, const double* __restrict__ A, const double* __restrict__ Rr,
-                                double* __restrict__ R) {
+                                double* __restrict__ R, int nsplit) {
   __shared__ double aW[kNA], bW[kNA];
   __shared__ double alpha[kMaxK][kNP], rv2[kMaxK][kNP], rw3[kMaxK][kNP];
-  const int c = blockIdx.x;
+  const int c = blockIdx.x / nsplit, part = blockIdx.x % nsplit;
   const int4 ch = cd.ch[c];
   const int l1 = ch.x, l2 = ch.y, l3 = ch.z;
   const double* G = cd.Ghat + ch.w;
@@ -241,7 +242,7 @@ __global__ void contract_kernel(Geo g, Dev d, ChanDev cd, const double* __restri
     const double* Az = A + zh * g.na_zh;  // point p of this (z, half): Az + p, component c at + c * sa
     const double* Rz = Rr + zh * g.nr_zh;
     // patch 1: one radial point per outer node, alpha summed over the inner node
-    for (int io = 0; io < g.Nx1; ++io) {
+    for (int io = part; io < g.Nx1; io += nsplit) {
       const double* rrec = Rz + io;
       double al = 0.0;  // thread k < K: alpha[k]
       for (int h0 = 0; h0 < g.Nh1; h0 += kNA) {
@@ -271,7 +272,7 @@ __global__ void contract_kernel(Geo g, Dev d, ChanDev cd, const double* __restri
     }
     // patch 2: every point is a radial point
     const int64_t n2 = (int64_t)g.Ny2 * g.Nh2;
-    for (int64_t p0 = 0; p0 < n2; p0 += kNP) {
+    for (int64_t p0 = (int64_t)part * kNP; p0 < n2; p0 += (int64_t)nsplit * kNP) {
       const int np = (int)min((int64_t)kNP, n2 - p0);
       __syncthreads();
       for (int i = t; i < np; i += blockDim.x)
@@ -299,8 +300,21 @@ __global__ void contract_kernel(Geo g, Dev d, ChanDev cd, const double* __restri
     const double f = cd.fscale[c];
     double* out = R + (((int64_t)c * K + k1) * K + k2) * K;
 #pragma unroll
-    for (int k3 = 0; k3 < K; ++k3) out[k3] += f * acc[k3];
+    for (int k3 = 0; k3 < K; ++k3) atomicAdd(out + k3, f * acc[k3]);
   }
+}
+
+template <int K>
+cudaError_t launch_contract_k(int NT, int threads, const Geo& g, const Dev& d, const ChanDev& cd, const double* A,
+                              const double* Rr, double* R) {
+  int dev = 0, sms = 1, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, contract_kernel<K>, threads, 0);
+  const int slots = sms * (per_sm > 0 ? per_sm : 1);
+  const int nsplit = std::max(1, (4 * slots + NT - 1) / NT);  // at least ~4 waves of CTAs
+  contract_kernel<K><<<NT * nsplit, threads>>>(g, d, cd, A, Rr, R, nsplit);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_contract(int K, int NT, int threads, const Geo& g, const Dev& d, const ChanDev& cd, const double* A,
@@ -308,15 +322,13 @@ cudaError_t launch_contract(int K, int NT, int threads, const Geo& g, const Dev&
   switch (K) {
 #define WEF_CK(k) \
   case k:         \
-    contract_kernel<k><<<NT, threads>>>(g, d, cd, A, Rr, R); \
-    break;
+    return launch_contract_k<k>(NT, threads, g, d, cd, A, Rr, R);
     WEF_CK(1) WEF_CK(2) WEF_CK(3) WEF_CK(4) WEF_CK(5) WEF_CK(6) WEF_CK(7) WEF_CK(8) WEF_CK(9) WEF_CK(10) WEF_CK(11)
     WEF_CK(12) WEF_CK(13) WEF_CK(14) WEF_CK(15) WEF_CK(16) WEF_CK(17)
 #undef WEF_CK
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <class T>

@@ -114,7 +114,10 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(RfCfg<K>::MAXREG)
   const int64_t nitems = ntiles * ntasks;
   // Accumulators in tensor memory: warp k1 uses lane quadrant k1 % 4 and columns from
   // (k1 / 4) * 2 * n1max on; one allocation for the CTA's lifetime.  Otherwise in
-  // shared memory.
+  // shared memory.  The launcher sizes the grid so that the resident CTAs' columns fit in
+  // the SM's 512; should the scheduler still place one more CTA on an SM, its allocation
+  // waits only until a resident CTA (which waits on nothing) has drained the queue and
+  // freed its columns.
   __shared__ uint32_t tbase_s;
   if constexpr (TMEM) {
     if (k1 == 0) {
