@@ -407,6 +407,14 @@ def bench_ragged(args, W, torch, dev, world, ncells=32768, seed=4):
     flops = sum(W.wef_flops(o.h, W.WEF_MIXED_TF32)[0] * n for o, n in zip(ops, counts))
     achieved = flops / (ms / 1e3) / 1e12
     W.wef_plan_destroy(plan)
+    # the same ragged batch through a radial-first plan (one persistent launch per shape on
+    # autotuned concurrent streams, graph-replayed), for comparison
+    rplan = W.wef_plan_create([o.h for o in ops], counts, W.WEF_RADIAL_FP32, 0)
+    rws = torch.empty(W.wef_plan_workspace_size(rplan), dtype=torch.uint8, device=dev)
+    rg = W.wef_plan_autotune(rplan, f.data_ptr(), q.data_ptr(), rws.data_ptr(), rws.numel(), st.cuda_stream)
+    rstep = lambda: W.wef_plan_graph_launch(rplan, f.data_ptr(), q.data_ptr(), rws.data_ptr(), rws.numel(), st.cuda_stream)  # noqa: E731
+    rms = _time_steps(rstep, args.steps, args.warmup, st, torch)
+    W.wef_plan_destroy(rplan)
     return _line("Q(f,f) cell-evals/s, ragged (Kmax,Lmax) in {6..16}^2", ncells / (ms / 1e3), "cells/s", ms, args, world,
                  "f64+tf32",
                  f"VHS gamma=0.5, {ncells} cells, (Kmax, Lmax) drawn independently per cell, 25 shapes grouped; one "
@@ -414,7 +422,10 @@ def bench_ragged(args, W, torch, dev, world, ncells=32768, seed=4):
                  + ("from the library quadrature" if real else "random stand-ins (timing does not depend on values)"),
                  roofline={"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": achieved / FP64_PEAK_TFLOPS, "fp64_flops_total": flops},
-                 gpu_launches=2 * args.steps)
+                 gpu_launches=2 * args.steps,
+                 radial_first={"cells_per_s": ncells / (rms / 1e3), "ms_per_step": rms, "fork_streams": rg,
+                               "note": "same batch, radial-first plan: per-shape persistent launches on concurrent "
+                                       "streams in one CUDA graph"})
 
 
 def bench_serve(args, W, torch, dev, world):

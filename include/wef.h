@@ -123,7 +123,11 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
  * first).  granularity = how many task ranges each 32-cell tile is split into
  * (0 = from the tuning cache named by the WEF_TUNE_CACHE environment variable,
  * else about 8 items per SM).  Precision: WEF_MIXED_TF32 or WEF_MIXED_BF16.
- * Every operator must have a core uploaded (Kmax >= 1) and must outlive the plan.
+ * With WEF_RADIAL_FP32 the plan runs the radial-first evaluation of each shape (one
+ * persistent launch per shape, largest first) on `granularity` concurrent forked
+ * streams (0 = cache, else 4), joined back to the caller's stream.
+ * Every operator must have a core uploaded (Kmax >= 1 for the tensor-core path) and
+ * must outlive the plan.
  * Set-up allocations happen in wef_plan_create only.
  */
 typedef struct wef_plan_s* wef_plan;
@@ -139,9 +143,9 @@ wef_status wef_plan_execute(wef_plan plan, const double* f_dev, double* q_dev, v
  * graph; later calls only launch it on `stream`. */
 wef_status wef_plan_graph_launch(wef_plan plan, const double* f_dev, double* q_dev, void* workspace,
                                  int64_t ws_bytes, void* stream);
-/* Autotuner: times the plan at granularities 1, 2, 4, ... on the given buffers
- * (synchronous), keeps the fastest, appends it to the WEF_TUNE_CACHE file if set,
- * and returns it in *chosen (may be NULL). */
+/* Autotuner: times the plan at granularities 1, 2, 4, ... (radial-first: 1, 2, 4, 8
+ * streams) on the given buffers (synchronous), keeps the fastest, appends it to the
+ * WEF_TUNE_CACHE file if set, and returns it in *chosen (may be NULL). */
 wef_status wef_plan_autotune(wef_plan plan, const double* f_dev, double* q_dev, void* workspace, int64_t ws_bytes,
                              void* stream, int* chosen);
 /* Synchronous check of the plan's device status word (see wef_device_status). */

@@ -51,6 +51,22 @@ cudaError_t launch_rf_tmem(int K, const float* ftile32, int* queue, double* q, i
                            const DevRadial& r, const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0,
                            cudaEvent_t ev1);
 
+cudaError_t prepare_rf(int K, int n1max) {
+  if (K < 1 || K > 17) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)n1max * 32 * K * sizeof(double);
+  if (2 * (smem + 1024) > 228 * 1024) return cudaSuccess;  // tensor-memory accumulators
+  switch (K) {
+#define WEF_RF(k) \
+  case k:         \
+    return rfk::prepare_rf_k<k, false>(smem);
+    WEF_RF(1) WEF_RF(2) WEF_RF(3) WEF_RF(4) WEF_RF(5) WEF_RF(6) WEF_RF(7) WEF_RF(8) WEF_RF(9) WEF_RF(10) WEF_RF(11)
+    WEF_RF(12) WEF_RF(13) WEF_RF(14) WEF_RF(15) WEF_RF(16) WEF_RF(17)
+#undef WEF_RF
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_rf(int K, const double* f, float* ftile32, int* queue, double* q, int64_t ncells, int NQ,
                       const DevRadial& r, const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0,
                       cudaEvent_t ev1) {

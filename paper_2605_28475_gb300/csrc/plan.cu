@@ -91,8 +91,19 @@ struct wef_plan_s {
   cudaGraphExec_t gexec = nullptr;
   const void *g_f = nullptr, *g_q = nullptr, *g_ws = nullptr;
   std::string key;
+  // radial-first plans: one evaluation per shape, spread over `nfork` forked streams
+  static constexpr int kMaxFork = 8;
+  std::vector<int64_t> rf_ws_off, rf_ws_len;
+  std::vector<int> rf_order;  // shapes by decreasing cost
+  cudaStream_t fork[kMaxFork] = {};
+  cudaEvent_t fork_ev[kMaxFork + 1] = {};
+  int nfork = 4;
 
   void release() {
+    for (auto& s : fork)
+      if (s) cudaStreamDestroy(s), s = nullptr;
+    for (auto& e : fork_ev)
+      if (e) cudaEventDestroy(e), e = nullptr;
     cudaFree(d_shapes);
     cudaFree(d_items);
     cudaFree(d_queue);
@@ -184,8 +195,33 @@ wef_status check_buffers(wef_plan_s* P, const double* f, double* q, void* ws, in
   return WEF_OK;
 }
 
+// Radial-first plan: the shapes' evaluations, largest first, round-robin over the forked
+// streams (fork from and join back to `s`, so the launch also captures into one graph).
+wef_status plan_launch_rf(wef_plan_s* P, const double* f, double* q, void* ws, cudaStream_t s) {
+  const int nf = std::max(1, std::min(P->nfork, wef_plan_s::kMaxFork));
+  cudaError_t e = cudaEventRecord(P->fork_ev[wef_plan_s::kMaxFork], s);
+  for (int i = 0; i < nf && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(P->fork[i], P->fork_ev[wef_plan_s::kMaxFork], 0);
+  if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("wef_plan: fork: ") + cudaGetErrorString(e));
+  int k = 0;
+  for (int si : P->rf_order) {
+    const RaggedShape& S = P->shapes[si];
+    if (S.ncells == 0) continue;
+    wef_status st = wef_evaluate(P->ops[si], f + S.f_off, q + S.q_off, S.ncells, WEF_RADIAL_FP32,
+                                 (char*)ws + P->rf_ws_off[si], P->rf_ws_len[si], P->fork[k % nf]);
+    if (st != WEF_OK) return st;
+    ++k;
+  }
+  for (int i = 0; i < nf && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(P->fork_ev[i], P->fork[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, P->fork_ev[i], 0);
+  }
+  if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("wef_plan: join: ") + cudaGetErrorString(e));
+  return WEF_OK;
+}
+
 wef_status plan_launch(wef_plan_s* P, const double* f, double* q, void* ws, cudaStream_t s) {
   if (P->total_cells == 0) return WEF_OK;
+  if (P->prec == WEF_RADIAL_FP32) return plan_launch_rf(P, f, q, ws, s);
   cudaError_t e = launch_ragged_tile_f(P->d_shapes, (int)P->shapes.size(), P->total_tiles, P->max_n, f, (double*)ws, s);
   if (e == cudaSuccess)
     e = launch_ragged_tc(P->prec == WEF_MIXED_TF32, P->max_k, P->nsm, P->d_shapes, P->d_items, P->nitems, P->d_queue,
@@ -202,13 +238,14 @@ wef_status wef_plan_create(const wef_op* ops, const int64_t* ncells, int nops, w
                            wef_plan* out) {
   if (!out || !ops || !ncells || nops <= 0) return set_error(WEF_EINVAL, "wef_plan_create: bad argument");
   *out = nullptr;
-  if (prec != WEF_MIXED_TF32 && prec != WEF_MIXED_BF16)
-    return set_error(WEF_EINVAL, "wef_plan_create: ragged plans run the tensor-core path (BF16 or TF32)");
+  const bool rf = prec == WEF_RADIAL_FP32;
+  if (prec != WEF_MIXED_TF32 && prec != WEF_MIXED_BF16 && !rf)
+    return set_error(WEF_EINVAL, "wef_plan_create: ragged plans run the tensor-core (BF16, TF32) or radial-first path");
   wef_plan_s* P = new (std::nothrow) wef_plan_s();
   if (!P) return set_error(WEF_ENOMEM, "wef_plan_create: host allocation failed");
   P->prec = prec;
   std::ostringstream key;
-  key << (prec == WEF_MIXED_TF32 ? "tf32" : "bf16");
+  key << (rf ? "rf32" : prec == WEF_MIXED_TF32 ? "tf32" : "bf16");
   int64_t tile0 = 0, fo = 0, wo = 0;
   for (int i = 0; i < nops; ++i) {
     wef_op op = ops[i];
@@ -220,7 +257,7 @@ wef_status wef_plan_create(const wef_op* ops, const int64_t* ncells, int nops, w
       delete P;
       return set_error(WEF_ENOCORE, "wef_plan_create: every operator needs an uploaded core");
     }
-    if (op->T.K < 2) {
+    if (op->T.K < 2 && !rf) {
       delete P;
       return set_error(WEF_ESHAPE, "wef_plan_create: the tensor-core path needs Kmax >= 1");
     }
@@ -254,6 +291,23 @@ wef_status wef_plan_create(const wef_op* ops, const int64_t* ncells, int nops, w
   }
   P->total_tiles = tile0;
   P->ws_bytes = wo * (int64_t)sizeof(double);
+  if (rf) {
+    // one radial-first workspace per shape (they run concurrently), 256-byte aligned
+    int64_t off = 0;
+    std::vector<double> cost;
+    for (size_t i = 0; i < P->ops.size(); ++i) {
+      int64_t b = 0;
+      wef_workspace_size(P->ops[i], P->ncells[i], WEF_RADIAL_FP32, &b);
+      b = std::max<int64_t>((b + 255) / 256 * 256, 256);
+      P->rf_ws_off.push_back(off);
+      P->rf_ws_len.push_back(b);
+      off += b;
+      cost.push_back((double)P->ncells[i] * (P->ops[i]->T.rprog.fp64_flops + P->ops[i]->T.rprog.fp32_flops / 64.0));
+      P->rf_order.push_back((int)i);
+    }
+    std::stable_sort(P->rf_order.begin(), P->rf_order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    P->ws_bytes = off;
+  }
   cudaDeviceProp prop;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -268,10 +322,30 @@ wef_status wef_plan_create(const wef_op* ops, const int64_t* ncells, int nops, w
   if (e == cudaSuccess) e = cudaMalloc((void**)&P->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(P->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+  for (int i = 0; rf && i < wef_plan_s::kMaxFork && e == cudaSuccess; ++i)
+    e = cudaStreamCreateWithFlags(&P->fork[i], cudaStreamNonBlocking);
+  for (int i = 0; rf && i <= wef_plan_s::kMaxFork && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&P->fork_ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     P->release();
     delete P;
     return set_error(WEF_ECUDA, std::string("wef_plan_create: ") + cudaGetErrorString(e));
+  }
+  if (rf) {
+    // the tuned quantity is the number of concurrent shape streams
+    int nf = granularity > 0 ? granularity : cache_lookup(P->key);
+    P->nfork = nf > 0 ? std::min(nf, (int)wef_plan_s::kMaxFork) : 4;
+    P->granularity = P->nfork;
+    // kernel attributes of every shape now, outside any later stream capture
+    for (size_t i = 0; i < P->ops.size() && e == cudaSuccess; ++i)
+      e = prepare_rf(P->ops[i]->T.K, P->ops[i]->T.rprog.n1max);
+    if (e != cudaSuccess) {
+      P->release();
+      delete P;
+      return set_error(WEF_ECUDA, std::string("wef_plan_create: ") + cudaGetErrorString(e));
+    }
+    *out = P;
+    return WEF_OK;
   }
   // granularity: explicit, cached from an earlier autotune, or enough items for ~8 per SM
   int g = granularity;
@@ -353,12 +427,23 @@ wef_status wef_plan_autotune(wef_plan plan, const double* f_dev, double* q_dev, 
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  const bool rf = plan->prec == WEF_RADIAL_FP32;
   int best_g = plan->granularity;
   float best = 1e30f;
   int max_tasks = 1;
   for (wef_op op : plan->ops) max_tasks = std::max(max_tasks, op->T.prog4.ntasks());
+  if (rf) max_tasks = wef_plan_s::kMaxFork;  // candidates: 1, 2, 4, 8 concurrent shape streams
   for (int g = 1; g <= 64 && g <= max_tasks; g *= 2) {
-    st = set_items(plan, g);
+    if (rf) {
+      plan->nfork = g;
+      plan->granularity = g;
+      if (plan->gexec) {
+        cudaGraphExecDestroy(plan->gexec);
+        plan->gexec = nullptr;
+      }
+    } else {
+      st = set_items(plan, g);
+    }
     if (st != WEF_OK) break;
     plan_launch(plan, f_dev, q_dev, workspace, s);  // warm-up
     cudaEventRecord(e0, s);
@@ -378,8 +463,16 @@ wef_status wef_plan_autotune(wef_plan plan, const double* f_dev, double* q_dev, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != WEF_OK) return st;
-  st = set_items(plan, best_g);
-  if (st != WEF_OK) return st;
+  if (rf) {
+    plan->nfork = plan->granularity = best_g;
+    if (plan->gexec) {
+      cudaGraphExecDestroy(plan->gexec);
+      plan->gexec = nullptr;
+    }
+  } else {
+    st = set_items(plan, best_g);
+    if (st != WEF_OK) return st;
+  }
   cache_store(plan->key, best_g);
   if (chosen) *chosen = best_g;
   return WEF_OK;

@@ -245,6 +245,14 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(RfCfg<K>::MAXREG)
   }
 }
 
+// Shared-memory opt-in of one instantiation (so that later launches, possibly under
+// stream capture, make no attribute calls).
+template <int K, bool TMEM>
+cudaError_t prepare_rf_k(size_t smem) {
+  static std::atomic<size_t> attr[kMaxDevices];
+  return smem > 0 ? smem_opt_in(rf_kernel<K, TMEM>, smem, attr) : cudaSuccess;
+}
+
 // Launches the persistent radial-first kernel (the queue was reset and the FP32 tiles
 // written by the caller).
 template <int K, bool TMEM>
@@ -261,9 +269,8 @@ cudaError_t launch_rf_k(const float* ftile32, int* queue, double* q, int64_t nce
     while (tcols < need) tcols <<= 1;
     if (tcols > 512) return cudaErrorInvalidValue;
   }
-  static std::atomic<size_t> attr[kMaxDevices];  // dynamic shared memory opted in, per device
-  if (smem > 0) {
-    cudaError_t e = smem_opt_in(rf_kernel<K, TMEM>, smem, attr);
+  {
+    cudaError_t e = prepare_rf_k<K, TMEM>(smem);
     if (e != cudaSuccess) return e;
   }
   int per_sm = 1;

@@ -60,6 +60,10 @@ void destroy_cublas(void* handle);
 // Radial-first FP32 core layout [sc][k1][k3][k2 -> KP4]: k2 padded to whole float4s.
 inline int rf_k2_padded(int K) { return (K + 3) / 4 * 4; }
 
+// Radial-first kernel attributes for operators of radial size K and largest shell n1max,
+// set ahead of launches that may be captured in a graph.
+cudaError_t prepare_rf(int K, int n1max);
+
 // Radial-first evaluation: FP32 re-tiling of f, then the persistent radial-first
 // kernel (queue reset here).  ftile32 and queue live in the caller's workspace.
 // ev0/ev1 (may be null) are recorded around the contraction kernel alone.

@@ -1,5 +1,5 @@
-"""Ragged batches through one persistent launch (wef_plan_*), checked against the per-shape
-evaluation (same arithmetic, so bit-identical) and against the oracle on sampled cells."""
+"""Ragged batches through plans (wef_plan_*), checked against the per-shape evaluation
+(same arithmetic, so bit-identical) and against the oracle on sampled cells."""
 import numpy as np
 import pytest
 
@@ -47,10 +47,13 @@ def _segments(q, shapes, counts):
     return out
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "rf32"])
 def test_ragged_equals_per_shape(prec):
-    shapes = [(2, 3), (4, 4), (6, 6), (3, 5), (16, 2)]
-    counts = [37, 64, 5, 100, 33]
+    """One plan over five shapes equals the per-shape evaluations bit for bit (tensor-core
+    paths: one persistent launch; radial-first: one launch per shape on forked streams),
+    also when replayed from its CUDA graph and after autotuning."""
+    shapes = [(2, 3), (4, 4), (6, 6), (3, 5), (16, 2)] + ([(0, 3)] if prec == "rf32" else [])
+    counts = [37, 64, 5, 100, 33] + ([9] if prec == "rf32" else [])
     ops, cores, fs = _setup(shapes, counts)
     f = _flat(fs)
     q = torch.full_like(f, float("nan"))
