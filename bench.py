@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--precision", default="rf32", choices=["fp64", "bf16", "tf32", "rf32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ncells", type=int, default=NCELLS)
+    ap.add_argument("--kl", type=int, default=KMAX, help="Kmax = Lmax of the main workload (default 12)")
     ap.add_argument("--cpu-sample-rows", type=int, default=384)
     ap.add_argument("--cpu-sample-cells", type=int, default=4)
     ap.add_argument("--workload", default="kl12",
@@ -475,7 +476,11 @@ def bench_serve(args, W, torch, dev, world):
 
 
 def main():
+    global KMAX, LMAX, METRIC
     args = parse()
+    if args.kl != KMAX:
+        KMAX = LMAX = args.kl
+        METRIC = f"Q(f,f) cell-evals/s at K=L={KMAX}"
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -615,7 +620,9 @@ def main():
             "workload": f"hard spheres (gamma=1), Kmax=Lmax={KMAX}, {ncells} cells per GPU, seeded two-Maxwellian "
                         f"mixtures, core from the library quadrature (pad 20/20)",
             "precision": args.precision,
-            "l2": "inputs (288 MB f + 288 MB Q) larger than L2, no flush",
+            "l2": (f"inputs ({ncells * (KMAX + 1) * (LMAX + 1) ** 2 * 8 / 1e6:.0f} MB f + the same in Q) "
+                   + ("larger than L2, no flush" if 2 * ncells * (KMAX + 1) * (LMAX + 1) ** 2 * 8 > 129e6
+                      else "smaller than L2 (not a headline configuration)")),
         },
         "roofline": {
             "bound": "alu",
@@ -628,7 +635,7 @@ def main():
             "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": TRAFFIC_BYTES.get(args.precision) if ncells == NCELLS else None,
+            "traffic": TRAFFIC_BYTES.get(args.precision) if (ncells == NCELLS and KMAX == 12) else None,
             "traffic_note": "DRAM bytes per launch (ncu); algorithmic: FP32 tiles in + FP64 Q out = 432 MB",
             "fp64_flops_per_cell": head["fp64_flops_per_cell"],
             "radial_flops_per_cell": head["radial_flops_per_cell"],

@@ -98,10 +98,14 @@ struct RfCfg {
   static constexpr int WARPS_PER_SMSP = (2 * K + 3) / 4;
   static constexpr int MAXREG_RAW = 16384 / (32 * WARPS_PER_SMSP) / 8 * 8;
   static constexpr int MAXREG = MAXREG_RAW > 255 ? 255 : MAXREG_RAW;
+  // The tensor-memory variant runs where the accumulators need more than half of an SM's
+  // 512 columns, i.e. one CTA per SM: it may use the whole register file.
+  static constexpr int MAXREG_1CTA_RAW = 16384 / (32 * ((K + 3) / 4)) / 8 * 8;
+  static constexpr int MAXREG_1CTA = MAXREG_1CTA_RAW > 255 ? 255 : MAXREG_1CTA_RAW;
 };
 
 template <int K, bool TMEM>
-__global__ void __launch_bounds__(32 * K) __maxnreg__(RfCfg<K>::MAXREG)
+__global__ void __launch_bounds__(32 * K) __maxnreg__(TMEM ? RfCfg<K>::MAXREG_1CTA : RfCfg<K>::MAXREG)
     rf_kernel(const float* __restrict__ ftile, double* __restrict__ qout, int64_t ncells, int64_t ntiles, int NQ,
               const int4* __restrict__ tasks, const int4* __restrict__ chans, const int4* __restrict__ blocks,
               const int4* __restrict__ uents, const double2* __restrict__ pw,
