@@ -54,7 +54,7 @@ cudaError_t launch_rf_tmem(int K, const float* ftile32, int* queue, double* q, i
 cudaError_t prepare_rf(int K, int n1max) {
   if (K < 1 || K > 17) return cudaErrorInvalidValue;
   const size_t smem = (size_t)n1max * 32 * K * sizeof(double);
-  if (2 * (smem + 1024) > 228 * 1024) return cudaSuccess;  // tensor-memory accumulators
+  if (rf_uses_tmem(K, n1max)) return cudaSuccess;  // tensor-memory accumulators
   switch (K) {
 #define WEF_RF(k) \
   case k:         \
@@ -76,10 +76,9 @@ cudaError_t launch_rf(int K, const double* f, float* ftile32, int* queue, double
   const int64_t ntiles = (ncells + 31) / 32;
   const int N = K * NQ;
   tile_f32_kernel<<<dim3((unsigned)ntiles, (unsigned)((N + 31) / 32)), dim3(32, 8), 0, s>>>(f, ftile32, ncells, K, NQ);
-  // shared-memory accumulators while two CTAs of them fit in the 228 KB of an SM
-  const size_t smem = (size_t)r.n1max * 32 * K * sizeof(double);
-  if (2 * (smem + 1024) > 228 * 1024)
-    return launch_rf_tmem(K, ftile32, queue, q, ncells, NQ, r, R32, nsm, s, ev0, ev1);
+  // shared-memory accumulators while two CTAs of them fit in the 228 KB of an SM (the
+  // program was built for the same choice: its q2 block width depends on it)
+  if (rf_uses_tmem(K, r.n1max)) return launch_rf_tmem(K, ftile32, queue, q, ncells, NQ, r, R32, nsm, s, ev0, ev1);
   switch (K) {
 #define WEF_RF(k) \
   case k:         \

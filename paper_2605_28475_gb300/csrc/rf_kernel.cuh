@@ -92,7 +92,7 @@ struct AccTmem {
 template <int K>
 struct RfCfg {
   static constexpr int KP4 = (K + 3) / 4 * 4;  // padded k2 (float4 core rows)
-  static constexpr int J = rf_group_width(K);   // q2 groups per block (register budget)
+  static constexpr int J = rf_group_width(K, false);  // q2 groups per block, shared-memory variant
   // Registers per thread that let two CTAs share an SM: each of the 4 sub-partitions has
   // 16384 registers and takes ceil(2 K / 4) of the two CTAs' warps.
   static constexpr int WARPS_PER_SMSP = (2 * K + 3) / 4;
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(TMEM ? RfCfg<K>::MAXREG_1C
               const int32_t* __restrict__ order, int ntasks, const float* __restrict__ R32, int* __restrict__ queue,
               int64_t group, int n1max, uint32_t tcols) {
   using Cfg = RfCfg<K>;
-  constexpr int J = Cfg::J, KP4 = Cfg::KP4, R4 = KP4 / 4, S = K * 32;
+  constexpr int J = rf_group_width(K, TMEM), KP4 = Cfg::KP4, R4 = KP4 / 4, S = K * 32;
   __shared__ int item_s;
   const int k1 = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nitems = ntiles * ntasks;

@@ -272,7 +272,7 @@ std::string build_tables(int kmax, int lmax, Tables& t) {
   {
     RadialProgram& RP = t.rprog;
     RP = RadialProgram();
-    const int K = t.K, J = rf_group_width(K);
+    const int K = t.K, J = rf_group_width(K, rf_uses_tmem(K, 2 * lmax + 1));
     RP.J = J;
     for (int l1 = 0; l1 <= lmax; ++l1) {
       const int q1b = l1 * l1, n1 = 2 * l1 + 1;

@@ -46,18 +46,21 @@ struct Program {
 #define WEF_HD
 #endif
 
-// q2 groups the radial-first kernel keeps in registers at once (its register budget).
-#ifndef WEF_RF_J13
-#define WEF_RF_J13 2  // for 10 <= K <= 13
-#endif
-WEF_HD constexpr int rf_group_width(int K) { return K <= 9 ? 4 : (K <= 13 ? WEF_RF_J13 : 1); }
+// Whether the radial-first kernel keeps the FP64 accumulators of the largest shell (n1max
+// targets) in tensor memory: when two CTAs' worth do not fit in an SM's shared memory.
+WEF_HD constexpr bool rf_uses_tmem(int K, int n1max) {
+  return 2 * ((long long)n1max * 32 * K * 8 + 1024) > 228LL * 1024;
+}
+// q2 groups the radial-first kernel keeps in registers at once: its register budget is
+// that of two CTAs per SM with shared-memory accumulators, of one with tensor memory.
+WEF_HD constexpr int rf_group_width(int K, bool tmem) { return K <= 9 ? 4 : (K <= 13 || tmem ? 2 : 1); }
 
 // Radial-first program (paper Sec. 4.5.3 ordering with a dense two-stage radial
 // contraction).  One task per output shell l1:
 //   tasks:  {q1_base, n1, chan_start, nchan}
 //   chans:  {sc, blk_start, nblk, 0}        symmetrised channel (l2 <= l3)
 //   blocks: two int4 per block: {nj, u_start, nu, 0}, {q2_0, q2_1, q2_2, q2_3}: up to
-//           J = rf_group_width(K) of the channel's q2 (the smaller shell), whose stage-1
+//           J = rf_group_width(K, tmem) of the channel's q2 (the smaller shell), whose stage-1
 //           products A(q2_j) are held together
 //   uents:  {q3 | mask << 16, pair_start, T_0 | T_1 << 16, T_2 | T_3 << 16}: each q3 paired
 //           with any q2 of the block, once; bit j of mask set if (q2_j, q3) is a pair, whose
