@@ -95,7 +95,10 @@ struct RfCfg {
   static constexpr int J = rf_group_width(K, false);  // q2 groups per block, shared-memory variant
   // Registers per thread that let two CTAs share an SM: each of the 4 sub-partitions has
   // 16384 registers and takes ceil(2 K / 4) of the two CTAs' warps.
-  static constexpr int WARPS_PER_SMSP = (2 * K + 3) / 4;
+  // CTAs per SM the register budget is sized for: about 32-36 resident warps where the
+  // accumulators of a Kmax = Lmax shell let that many CTAs share the shared memory
+  static constexpr int CTAS = rf_ctas_per_sm(K);
+  static constexpr int WARPS_PER_SMSP = (CTAS * K + 3) / 4;
   static constexpr int MAXREG_RAW = 16384 / (32 * WARPS_PER_SMSP) / 8 * 8;
   static constexpr int MAXREG = MAXREG_RAW > 255 ? 255 : MAXREG_RAW;
   // The tensor-memory variant runs where the accumulators need more than half of an SM's

@@ -53,7 +53,15 @@ WEF_HD constexpr bool rf_uses_tmem(int K, int n1max) {
 }
 // q2 groups the radial-first kernel keeps in registers at once: its register budget is
 // that of two CTAs per SM with shared-memory accumulators, of one with tensor memory.
-WEF_HD constexpr int rf_group_width(int K, bool tmem) { return K <= 9 ? 4 : (K <= 13 || tmem ? 2 : 1); }
+// CTAs per SM the shared-memory variant's register budget is sized for: about 32-36
+// warps for K <= 9 (measured at K = 9: 3.63M cells/s with 4 CTAs of 56 registers against
+// 2.81M with 2 of 96); two from K = 10 on, where the tighter budget spills (-2 to -5%).
+WEF_HD constexpr int rf_ctas_per_sm(int K) {
+  return K <= 4 ? 8 : K == 5 ? 7 : K == 6 ? 6 : K == 7 ? 5 : K <= 9 ? 4 : 2;
+}
+WEF_HD constexpr int rf_group_width(int K, bool tmem) {
+  return tmem ? (K <= 9 ? 4 : 2) : (K <= 4 ? 4 : K <= 13 ? 2 : 1);
+}
 
 // Radial-first program (paper Sec. 4.5.3 ordering with a dense two-stage radial
 // contraction).  One task per output shell l1:
