@@ -42,6 +42,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # (K=L=12, 16384 cells), from a one-pass ncu capture of `bench.py --steps 1 --warmup 1
 # --precision rf32` (dram__bytes_read.sum 398.05 MB + dram__bytes_write.sum 325.89 MB).
 TRAFFIC_BYTES = {"rf32": 723.94e6}
+# arithmetic types of each path: FP64 reductions and projection, plus the radial products'
+DTYPES = {"fp64": "f64", "bf16": "f64+bf16", "tf32": "f64+tf32", "rf32": "f64+f32"}
 
 
 def parse():
@@ -363,7 +365,7 @@ def bench_rk4(args, W, torch, dev, world, ncells=16384, nrk=4):
     out = torch.empty_like(d)
     lstep = lambda: op.linearized_apply(f0, d, out, precision=prec)  # noqa: E731
     ms_l = _time_steps(lstep, args.steps, args.warmup, st, torch)
-    dtype = "f64" if args.precision == "fp64" else f"f64+{args.precision}"
+    dtype = DTYPES[args.precision]
     return _line("RK4 cell-steps/s at K=L=12", ncells * nrk / (ms / 1e3), "cell-steps/s", ms, args, world, dtype,
                  f"hard spheres, Kmax=Lmax=12, {ncells} two-Maxwellian cells, {nrk} RK4 steps (dt=1e-3) per timed "
                  f"step, {args.precision} evaluations",
@@ -483,7 +485,7 @@ def bench_serve(args, W, torch, dev, world):
     srv = serve.Server(ops, arena_bytes=24 << 30, nslots=8, precision=args.precision, device=str(dev),
                        cost_per_cell={sh: 1.0 / c for sh, c in cap.items()}, max_batch_s=0.05)
     res = serve.run(srv, reqs)
-    dtype = "f64" if args.precision == "fp64" else f"f64+{args.precision}"
+    dtype = DTYPES[args.precision]
     return _line("serve: p50/p99 latency and cells/s", res["cells_per_s"], "cells/s", None, args, world, dtype,
                  f"Poisson arrivals at 0.7x capacity ({rate:.1f} req/s) for {args.duration:.0f} s; sizes log-uniform "
                  f"1-{max_cells} cells; Kmax=Lmax in {{8,10,12,16}}; 8 stream slots; 24 GiB admission arena; "
@@ -630,7 +632,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else f"f64+{args.precision}",
+        "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {
             "workload": f"hard spheres (gamma=1), Kmax=Lmax={KMAX}, {ncells} cells per GPU, seeded two-Maxwellian "
