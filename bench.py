@@ -42,7 +42,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # (K=L=12, 16384 cells), from a one-pass ncu capture of `bench.py --steps 1 --warmup 1
 # --precision rf32` (dram__bytes_read.sum 398.05 MB + dram__bytes_write.sum 325.89 MB).
 TRAFFIC_BYTES = {"rf32": 723.94e6}
-# arithmetic types of each path: FP64 reductions and projection, plus the radial products'
+# arithmetic types of each path: FP64 reductions and projection, plus the radial products
 DTYPES = {"fp64": "f64", "bf16": "f64+bf16", "tf32": "f64+tf32", "rf32": "f64+f32"}
 
 
