@@ -141,9 +141,9 @@ def cpu_angular_first(sample_cells=32, seed=3):
     t0 = time.perf_counter()
     angular_first.evaluate(KMAX, LMAX, R, f, sl=sl)
     dt = time.perf_counter() - t0
-    return {"value": sample_cells / dt, "unit": "cells/s", "cores": os.cpu_count(),
+    return {"value": sample_cells / dt, "unit": "cells/s", "cores": 1,
             "kind": "angular-first numpy (Sec. 4.5.4)",
-            "sample": f"{sample_cells} cells, {dt:.1f} s; numpy threads default"}
+            "sample": f"{sample_cells} cells, {dt:.1f} s; numpy einsum without BLAS: one thread"}
 
 
 class ClockSampler:
