@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <limits>
 #include <map>
 #include <set>
 
@@ -75,9 +76,19 @@ double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3) {
 
 namespace {
 
+// 3j(l1 l2 l3; 0 0 0) for l <= 20, computed once per thread and triple.
+double wigner3j_000(int l1, int l2, int l3) {
+  constexpr int kL = 21;
+  if (l1 >= kL || l2 >= kL || l3 >= kL) return wigner3j(l1, l2, l3, 0, 0, 0);
+  thread_local std::vector<double> cache(kL * kL * kL, std::numeric_limits<double>::quiet_NaN());
+  double& v = cache[(l1 * kL + l2) * kL + l3];
+  if (std::isnan(v)) v = wigner3j(l1, l2, l3, 0, 0, 0);
+  return v;
+}
+
 double complex_gaunt(int l1, int m1, int l2, int m2, int l3, int m3) {
   if (m1 + m2 + m3 != 0) return 0.0;
-  const double t0 = wigner3j(l1, l2, l3, 0, 0, 0);
+  const double t0 = wigner3j_000(l1, l2, l3);
   if (t0 == 0.0) return 0.0;
   return std::sqrt((2.0 * l1 + 1) * (2.0 * l2 + 1) * (2.0 * l3 + 1) / (4.0 * M_PI)) * t0 *
          wigner3j(l1, l2, l3, m1, m2, m3);
@@ -115,11 +126,29 @@ double real_gaunt(int l1, int m1, int l2, int m2, int l3, int m3) {
   std::complex<double> u1[2], u2[2], u3[2];
   const int n1 = real_to_complex(m1, mu1, u1), n2 = real_to_complex(m2, mu2, u2), n3 = real_to_complex(m3, mu3, u3);
   std::complex<double> acc = 0.0;
+  // complex Gaunt values already computed in this call; G(-mu) = (-1)^(l1+l2+l3) G(mu)
+  int seen_mu[8][2];
+  double seen_g[8];
+  int nseen = 0;
+  const double parity = ((l1 + l2 + l3) & 1) ? -1.0 : 1.0;
   for (int a = 0; a < n1; ++a)
     for (int b = 0; b < n2; ++b)
       for (int c = 0; c < n3; ++c) {
         if (mu1[a] + mu2[b] + mu3[c] != 0) continue;
-        acc += u1[a] * u2[b] * u3[c] * complex_gaunt(l1, mu1[a], l2, mu2[b], l3, mu3[c]);
+        double G = 0.0;
+        bool found = false;
+        for (int i = 0; i < nseen && !found; ++i)
+          if (seen_mu[i][0] == -mu1[a] && seen_mu[i][1] == -mu2[b]) {
+            G = parity * seen_g[i];
+            found = true;
+          }
+        if (!found) {
+          G = complex_gaunt(l1, mu1[a], l2, mu2[b], l3, mu3[c]);
+          seen_mu[nseen][0] = mu1[a];
+          seen_mu[nseen][1] = mu2[b];
+          seen_g[nseen++] = G;
+        }
+        acc += u1[a] * u2[b] * u3[c] * G;
       }
   return acc.real();
 }
