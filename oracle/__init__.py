@@ -22,6 +22,7 @@ angular_first
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` against closed forms or values printed in the paper
-(Table 1, Table 3, Table 5, Table 6), except the VHS (gamma=0.5) core, which the
-paper does not pin beyond conservation: "parity unpinned" for gamma not in {0, 1}.
+(Table 1, Table 3, Table 5, Table 6).  The core for any power law u^gamma (Maxwell,
+VHS gamma=0.5, hard spheres) is also pinned entry by entry to an exact 8D evaluation of
+the weak form in centre-of-mass and relative velocity at small (Kmax, Lmax).
 """

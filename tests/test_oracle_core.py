@@ -126,6 +126,61 @@ def test_bruteforce_8d_maxwell():
     assert np.max(np.abs(C - C_fact)) < 1e-13 * np.max(np.abs(C))
 
 
+@pytest.mark.parametrize("km,lm", [(1, 2), (2, 1)])
+@pytest.mark.parametrize("gamma", [0.0, 0.5, 1.0])
+def test_bruteforce_8d_any_gamma(gamma, km, lm):
+    """The same weak form for any power law u^gamma, exact at small (Kmax, Lmax).
+
+    Centre of mass V = (v + w)/2 and relative velocity g = v - w (unit Jacobian) split the
+    Maxwellian pair weight into e^{-|V|^2} e^{-|g|^2/4}, and u^gamma = |g|^gamma becomes part
+    of the radial weight of g.  Every test function is a polynomial in (V, g, |g| sigma), so
+    after exact sphere rules over g/|g| and sigma (which annihilate the odd powers of |g|) the
+    radial integrand is an even polynomial in |g|: with s = |g|^2/4 the generalized
+    Gauss-Laguerre rule of weight s^{(1+gamma)/2} e^{-s} integrates it exactly.  Independent of
+    the oracle's Duffy-patched (z, x, y) quadrature; this pins the VHS core (gamma = 0.5) and
+    the hard-sphere core (gamma = 1) entry by entry, raw, before any zeroing."""
+    K, NQ = km + 1, (lm + 1) ** 2
+    N = K * NQ
+    lq = np.array([basis.lm_of_q(q)[0] for q in range(NQ)])
+    op = dense.DenseOperator(km, lm, core.core(km, lm, gamma))
+    C_fact = np.stack([op.slice(a) for a in range(N)])
+
+    def phi(p):
+        r = np.linalg.norm(p, axis=-1)
+        Y = basis.real_sh_all(lm, p / np.maximum(r, 1e-300)[..., None])
+        Rr = basis.radial_all(K, lm, r)[..., lq]  # [..., K, NQ]
+        return (Rr * Y[..., None, :]).reshape(p.shape[:-1] + (N,))
+
+    deg = 2 * (2 * km + lm)  # degree of phi_b(v) phi_c(w) in g
+    # V: weight pi^{-3/2} e^{-|V|^2}, i.e. x / sqrt 2 with x standard normal per axis; the
+    # integrand has degree deg + 2 km + lm in V
+    x, wx = np.polynomial.hermite_e.hermegauss((deg + 2 * km + lm) // 2 + 1)
+    wx = wx / math.sqrt(2 * math.pi)
+    Vn = np.stack(np.meshgrid(x, x, x, indexing="ij"), -1).reshape(-1, 3) / math.sqrt(2.0)
+    Vw = np.einsum("i,j,k->ijk", wx, wx, wx).reshape(-1)
+    # g = 2 sqrt(s) ghat: (4 pi)^{-3/2} e^{-|g|^2/4} |g|^gamma dg
+    #   = (4 pi)^{-3/2} 2^{2+gamma} s^{(1+gamma)/2} e^{-s} ds dghat
+    s, ws = special.roots_genlaguerre((deg + 2 * km + lm) // 2 + 1, 0.5 * (1.0 + gamma))
+    ws = ws * 2.0 ** (2.0 + gamma) * (4 * math.pi) ** -1.5
+    gh, wgh = gaunt.sphere_rule(deg + 2 * km + lm + 1)
+    g = (2.0 * np.sqrt(s))[:, None, None] * gh[None, :, :]  # [S, G, 3]
+    gw = (ws[:, None] * wgh[None, :]).reshape(-1)
+    g = g.reshape(-1, 3)
+    r = np.linalg.norm(g, axis=1)
+    sph, sw = gaunt.sphere_rule(2 * km + lm + 1)
+    sw = sw / (4 * math.pi)  # B = u^gamma / (4 pi); u^gamma is in the g weight
+    C = np.zeros((N, N, N))
+    for V, wV in zip(Vn, Vw):
+        v, w = V + 0.5 * g, V - 0.5 * g
+        pv, pw = phi(v), phi(w)
+        vp = V[None, None, :] + 0.5 * r[:, None, None] * sph[None, :, :]
+        gain = np.einsum("s,psa->pa", sw, phi(vp))
+        loss = pv * sw.sum()
+        G = (gain - loss) * (wV * gw)[:, None]
+        C += ((G[:, :, None] * pv[:, None, :]).reshape(len(gw), N * N).T @ pw).reshape(N, N, N)
+    assert np.max(np.abs(C - C_fact)) < 1e-13 * np.max(np.abs(C))
+
+
 # ----------------------------------------------------------------- hard spheres
 def test_chapman_enskog_viscosity_table5():
     """Table 5: f_mu = L_00 [L^{-1}]_00 of the l = 2 block for hard spheres; Kmax = 1 is 205/202."""
