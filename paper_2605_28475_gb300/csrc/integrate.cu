@@ -63,7 +63,8 @@ wef_status wef_integrate(wef_op op, double* f_dev, int64_t ncells, double dt, in
   if (ncells == 0 || nsteps == 0) return WEF_OK;
   if (!f_dev || !workspace) return wef::set_error(WEF_EINVAL, "wef_integrate: NULL buffer");
   int64_t need = 0, n = 0, ev = 0;
-  wef_integrate_workspace_size(op, ncells, prec, &need);
+  wef_status st0 = wef_integrate_workspace_size(op, ncells, prec, &need);
+  if (st0 != WEF_OK) return st0;
   if (ws_bytes < need) return wef::set_error(WEF_EINVAL, "wef_integrate: workspace too small");
   wef_sizes(op, &n, nullptr, nullptr, nullptr);
   wef_workspace_size(op, ncells, prec, &ev);
@@ -98,7 +99,8 @@ wef_status wef_linearized_apply(wef_op op, const double* c0_dev, const double* d
   if (!c0_dev || !d_dev || !out_dev || !workspace)
     return wef::set_error(WEF_EINVAL, "wef_linearized_apply: NULL buffer");
   int64_t need = 0, n = 0, ev = 0;
-  wef_integrate_workspace_size(op, ncells, prec, &need);
+  wef_status st0 = wef_integrate_workspace_size(op, ncells, prec, &need);
+  if (st0 != WEF_OK) return st0;
   if (ws_bytes < need) return wef::set_error(WEF_EINVAL, "wef_linearized_apply: workspace too small");
   wef_sizes(op, &n, nullptr, nullptr, nullptr);
   wef_workspace_size(op, ncells, prec, &ev);

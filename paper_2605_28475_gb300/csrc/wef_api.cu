@@ -135,6 +135,11 @@ wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigne
   const int64_t K3 = (int64_t)K * K * K;
   const int64_t NT = (int64_t)T.chans.size();
   if (len != NT * K3) return fail(WEF_ESHAPE, "wef_upload_core: len must be N_T*K^3");
+  if (op->d_status) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != op->device)
+      return fail(WEF_EINVAL, "wef_upload_core: the current device is not the one the operator was set up on");
+  }
   cudaError_t de = ensure_device(op);
   if (de != cudaSuccess) return cuda_fail(de, "wef_upload_core: device set-up");
   std::vector<double> R(R_host, R_host + len);
@@ -204,6 +209,7 @@ wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigne
 
 wef_status wef_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int64_t* bytes) {
   if (!op || !bytes || ncells < 0) return fail(WEF_EINVAL, "wef_workspace_size: bad argument");
+  if (!valid_precision(prec)) return fail(WEF_EINVAL, "wef_workspace_size: unknown precision");
   const int64_t ntiles = (ncells + 31) / 32;
   const int64_t tile_elems = ntiles * 32 * (int64_t)op->T.K * op->T.NQ;
   *bytes = tile_elems * (int64_t)sizeof(double);
@@ -218,13 +224,14 @@ wef_status wef_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int
 wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t ncells, wef_precision prec,
                         void* workspace, int64_t workspace_bytes, void* stream) {
   if (!op) return fail(WEF_EINVAL, "wef_evaluate: op is NULL");
+  if (!valid_precision(prec)) return fail(WEF_EINVAL, "wef_evaluate: unknown precision");
   if (ncells < 0) return fail(WEF_EINVAL, "wef_evaluate: ncells < 0");
   if (ncells == 0) return WEF_OK;
   if (!f_dev || !q_dev || !workspace) return fail(WEF_EINVAL, "wef_evaluate: NULL buffer");
   if (!op->has_core) return fail(WEF_ENOCORE, "wef_evaluate: no core uploaded");
   if (((uintptr_t)workspace & 255) != 0) return fail(WEF_EINVAL, "wef_evaluate: workspace not 256-byte aligned");
   int64_t need = 0;
-  wef_workspace_size(op, ncells, prec, &need);
+  if (wef_workspace_size(op, ncells, prec, &need) != WEF_OK) return WEF_EINVAL;
   if (workspace_bytes < need) return fail(WEF_EINVAL, "wef_evaluate: workspace too small");
   if (ncells > (int64_t)65535 * 32 * 1024) return fail(WEF_EINVAL, "wef_evaluate: ncells too large");
   {
@@ -247,8 +254,6 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
   double* ftile = (double*)workspace;
   cudaError_t e = launch_tile_f(f_dev, ftile, ncells, K, NQ, s);
   if (e != cudaSuccess) return cuda_fail(e, "wef_evaluate: tile kernel");
-  if (prec != WEF_FP64 && prec != WEF_MIXED_BF16 && prec != WEF_MIXED_TF32)
-    return fail(WEF_EINVAL, "wef_evaluate: unknown precision");  // (radial-first handled above)
   // chunk count: enough CTAs for several waves of the GPU
   const int v = prec == WEF_FP64 ? 0 : 1;
   const wef_operator::DevProg& D = op->dp[v];
@@ -281,6 +286,7 @@ wef_status wef_core_build(wef_op op, int pad_rad, int pad_ang, double* R_out, in
 
 wef_status wef_flops(wef_op op, wef_precision prec, double* fp64_flops_per_cell, double* tc_flops_per_cell) {
   if (!op) return fail(WEF_EINVAL, "wef_flops: op is NULL");
+  if (!valid_precision(prec)) return fail(WEF_EINVAL, "wef_flops: unknown precision");
   if (prec == WEF_RADIAL_FP32) {
     if (fp64_flops_per_cell) *fp64_flops_per_cell = op->T.rprog.fp64_flops;
     if (tc_flops_per_cell) *tc_flops_per_cell = op->T.rprog.fp32_flops;

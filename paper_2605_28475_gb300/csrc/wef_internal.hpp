@@ -12,6 +12,11 @@
 
 namespace wef {
 
+// One of the four evaluation precisions of wef_precision.
+inline bool valid_precision(wef_precision p) {
+  return p == WEF_FP64 || p == WEF_MIXED_BF16 || p == WEF_MIXED_TF32 || p == WEF_RADIAL_FP32;
+}
+
 // Device copy of one Program (see tables.hpp).
 struct DevProgram {
   const int32_t* prog = nullptr;

@@ -86,5 +86,16 @@ def test_argument_errors():
             W.wef_workspace_size(h, -1)
         assert W.wef_workspace_size(h, 0) == 0
         assert W.wef_workspace_size(h, 33) == 64 * 3 * 9 * 8
+        # an unknown precision is refused before any size is computed or any work queued
+        for fn in (W.wef_workspace_size, W.wef_integrate_workspace_size, W.wef_host_workspace_size):
+            with pytest.raises(W.WefError) as e:
+                fn(h, 33, 7)
+            assert e.value.status == W.WEF_EINVAL
+        with pytest.raises(W.WefError) as e:
+            W.wef_flops(h, 7)
+        assert e.value.status == W.WEF_EINVAL
+        with pytest.raises(W.WefError) as e:
+            W.wef_evaluate(h, 0, 0, 0, 7, 0, 0, 0)
+        assert e.value.status == W.WEF_EINVAL and "precision" in str(e.value)
     finally:
         W.wef_destroy(h)
