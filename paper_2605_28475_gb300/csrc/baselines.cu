@@ -139,6 +139,8 @@ wef_status wef_naive_evaluate(wef_op op, const double* f_dev, double* q_dev, int
   if (ncells == 0) return WEF_OK;
   if (!f_dev || !q_dev || !workspace) return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: NULL buffer");
   if (!op->has_core) return wef::set_error(WEF_ENOCORE, "wef_naive_evaluate: no core uploaded");
+  if (((uintptr_t)workspace & 255) != 0)
+    return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: workspace not 256-byte aligned");
   int64_t need = 0;
   wef_workspace_size(op, ncells, WEF_FP64, &need);
   if (ws_bytes < need) return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: workspace too small");

@@ -203,18 +203,22 @@ wef_status plan_launch_rf(wef_plan_s* P, const double* f, double* q, void* ws, c
   for (int i = 0; i < nf && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(P->fork[i], P->fork_ev[wef_plan_s::kMaxFork], 0);
   if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("wef_plan: fork: ") + cudaGetErrorString(e));
   int k = 0;
+  wef_status st = WEF_OK;
   for (int si : P->rf_order) {
     const RaggedShape& S = P->shapes[si];
     if (S.ncells == 0) continue;
-    wef_status st = wef_evaluate(P->ops[si], f + S.f_off, q + S.q_off, S.ncells, WEF_RADIAL_FP32,
-                                 (char*)ws + P->rf_ws_off[si], P->rf_ws_len[si], P->fork[k % nf]);
-    if (st != WEF_OK) return st;
+    st = wef_evaluate(P->ops[si], f + S.f_off, q + S.q_off, S.ncells, WEF_RADIAL_FP32,
+                      (char*)ws + P->rf_ws_off[si], P->rf_ws_len[si], P->fork[k % nf]);
+    if (st != WEF_OK) break;
     ++k;
   }
+  // join every fork even after a failure, so that a stream capture never ends with
+  // unjoined work
   for (int i = 0; i < nf && e == cudaSuccess; ++i) {
     e = cudaEventRecord(P->fork_ev[i], P->fork[i]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, P->fork_ev[i], 0);
   }
+  if (st != WEF_OK) return st;
   if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("wef_plan: join: ") + cudaGetErrorString(e));
   return WEF_OK;
 }
@@ -424,9 +428,13 @@ wef_status wef_plan_autotune(wef_plan plan, const double* f_dev, double* q_dev, 
   wef_status st = check_buffers(plan, f_dev, q_dev, workspace, ws_bytes);
   if (st != WEF_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return set_error(WEF_ECUDA, std::string("wef_plan_autotune: ") + cudaGetErrorString(ce));
+  }
   const bool rf = plan->prec == WEF_RADIAL_FP32;
   int best_g = plan->granularity;
   float best = 1e30f;
@@ -445,9 +453,10 @@ wef_status wef_plan_autotune(wef_plan plan, const double* f_dev, double* q_dev, 
       st = set_items(plan, g);
     }
     if (st != WEF_OK) break;
-    plan_launch(plan, f_dev, q_dev, workspace, s);  // warm-up
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < 2; ++r) plan_launch(plan, f_dev, q_dev, workspace, s);
+    st = plan_launch(plan, f_dev, q_dev, workspace, s);  // warm-up
+    if (st == WEF_OK) cudaEventRecord(e0, s);
+    for (int r = 0; r < 2 && st == WEF_OK; ++r) st = plan_launch(plan, f_dev, q_dev, workspace, s);
+    if (st != WEF_OK) break;
     cudaEventRecord(e1, s);
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       st = set_error(WEF_ECUDA, "wef_plan_autotune: timing failed");
