@@ -172,8 +172,18 @@ class Server:
                 staging.append(pinned)
                 r.admitted = now
                 off += n
-            wef_evaluate(self.ops[shape].h, self.arena.ptr(fo), self.arena.ptr(qo), cells, self.prec,
-                         self.arena.ptr(wo), wn, st.cuda_stream)
+            try:
+                wef_evaluate(self.ops[shape].h, self.arena.ptr(fo), self.arena.ptr(qo), cells, self.prec,
+                             self.arena.ptr(wo), wn, st.cuda_stream)
+            except Exception:
+                # the evaluation was refused or failed to launch: once the work already
+                # queued on the slot has finished, return the memory to the arena and the
+                # requests to the front of the queue
+                st.synchronize()
+                for o, ln in allocs:
+                    self.arena.release(o, ln)
+                waiting[:0] = chosen
+                raise
             ev = torch.cuda.Event()
             ev.record(st)
         self.slot_busy[slot] = (chosen, ev, allocs, staging)
