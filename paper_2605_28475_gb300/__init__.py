@@ -249,8 +249,26 @@ def wef_destroy(op):
     _check(lib().wef_destroy(op))
 
 
+def _cells_arg(t, n_per_cell, name, cuda=True, device=None):
+    """Number of cells of a [ncells, K, NQ] (or [ncells, K * NQ]) float64 tensor, after
+    checking what the library cannot: dtype, contiguity, placement and the per-cell size
+    (a tensor shaped for another operator would be read or written past its end)."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 tensor")
+    if t.is_cuda != cuda or (device is not None and t.device != device):
+        raise ValueError(f"{name} must be on {device if device is not None else ('a CUDA device' if cuda else 'the host')}")
+    if t.dim() < 1 or t.numel() != t.shape[0] * n_per_cell:
+        raise ValueError(f"{name} must hold {n_per_cell} doubles per cell, got shape {tuple(t.shape)}")
+    return t.shape[0]
+
+
 class Operator:
-    """Owns a wef_op; evaluates Q(f, f) on torch CUDA tensors [ncells, K, NQ] float64."""
+    """Owns a wef_op; evaluates Q(f, f) on torch CUDA tensors [ncells, K, NQ] float64.
+
+    The helper keeps one workspace per kind of call and reuses it: calls made through the
+    same Operator on different streams must be ordered by the caller."""
 
     def __init__(self, kmax, lmax, gamma):
         self.kmax, self.lmax, self.gamma = kmax, lmax, gamma
@@ -279,10 +297,11 @@ class Operator:
         import torch
 
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        assert f.is_cuda and f.dtype == torch.float64 and f.is_contiguous()
-        ncells = f.shape[0]
+        ncells = _cells_arg(f, self.N, "f")
         if q is None:
             q = torch.empty_like(f)
+        elif _cells_arg(q, self.N, "q", device=f.device) != ncells:
+            raise ValueError("q must have as many cells as f")
         ws = self.workspace(ncells, prec, f.device)
         st = stream if stream is not None else torch.cuda.current_stream(f.device)
         wef_evaluate(self.h, f.data_ptr(), q.data_ptr(), ncells, prec, ws.data_ptr(), ws.numel(), st.cuda_stream)
@@ -302,7 +321,7 @@ class Operator:
         import torch
 
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        assert f.is_cuda and f.dtype == torch.float64 and f.is_contiguous()
+        _cells_arg(f, self.N, "f")
         ws = self._dyn_workspace(f.shape[0], prec, f.device)
         st = stream if stream is not None else torch.cuda.current_stream(f.device)
         wef_integrate(self.h, f.data_ptr(), f.shape[0], dt, nsteps, prec, ws.data_ptr(), ws.numel(), st.cuda_stream)
@@ -313,11 +332,13 @@ class Operator:
         import torch
 
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        for t in (c0, d):
-            assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
-        assert c0.shape == d.shape
+        ncells = _cells_arg(d, self.N, "d")
+        if _cells_arg(c0, self.N, "c0", device=d.device) != ncells:
+            raise ValueError("c0 and d must have the same number of cells")
         if out is None:
             out = torch.empty_like(d)
+        elif _cells_arg(out, self.N, "out", device=d.device) != ncells:
+            raise ValueError("out must have as many cells as d")
         ws = self._dyn_workspace(d.shape[0], prec, d.device)
         st = stream if stream is not None else torch.cuda.current_stream(d.device)
         wef_linearized_apply(self.h, c0.data_ptr(), d.data_ptr(), out.data_ptr(), d.shape[0], prec, ws.data_ptr(),
@@ -331,9 +352,11 @@ class Operator:
         import torch
 
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        assert not f.is_cuda and f.dtype == torch.float64 and f.is_contiguous()
+        ncells = _cells_arg(f, self.N, "f", cuda=False)
         if q is None:
             q = torch.empty_like(f, pin_memory=f.is_pinned())
+        elif _cells_arg(q, self.N, "q", cuda=False) != ncells:
+            raise ValueError("q must have as many cells as f")
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         need = wef_host_workspace_size(self.h, chunk_cells, prec)
         ws = getattr(self, "_hws", None)

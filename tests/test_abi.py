@@ -99,3 +99,29 @@ def test_argument_errors():
         assert e.value.status == W.WEF_EINVAL and "precision" in str(e.value)
     finally:
         W.wef_destroy(h)
+
+
+def test_binding_rejects_mis_shaped_tensors():
+    """The Python helper refuses tensors the library would read or write past their end
+    (another operator's per-cell size), wrong dtypes, non-contiguous views and tensors on
+    the wrong side of the bus, before any CUDA call."""
+    torch = pytest.importorskip("torch")
+    op = W.Operator(2, 2, 0.0)  # 3 x 9 = 27 doubles per cell
+    try:
+        ok = torch.zeros(4, 3, 9, dtype=torch.float64)
+        bad = [torch.zeros(4, 3, 4, dtype=torch.float64),           # another Lmax
+               torch.zeros(4, 27, dtype=torch.float32),             # dtype
+               torch.zeros(4, 9, 3, dtype=torch.float64).transpose(1, 2)]  # not contiguous
+        for f in bad:
+            with pytest.raises(ValueError):
+                op.evaluate_host(f)
+        with pytest.raises(ValueError):
+            op.evaluate_host(ok, q=torch.zeros(3, 3, 9, dtype=torch.float64))
+        with pytest.raises(ValueError):
+            op.evaluate(ok)  # host tensor given to the device entry point
+        with pytest.raises(ValueError):
+            op.linearized_apply(ok, ok)
+        with pytest.raises(ValueError):
+            op.integrate(ok, 0.1, 1)
+    finally:
+        op.close()
