@@ -654,7 +654,9 @@ def main():
             "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": TRAFFIC_BYTES.get(args.precision) if (ncells == NCELLS and KMAX == 12) else None,
-            "traffic_note": "DRAM bytes per launch (ncu); algorithmic: FP32 tiles in + FP64 Q out = 432 MB",
+            "traffic_note": ("DRAM bytes per launch (one-pass ncu capture at 16384 cells); algorithmic: FP32 tiles "
+                             "in + FP64 Q out = 432 MB. Captured before q2 groups were paired by shared q3 "
+                             "(same kernel code, its program then had 32707 instead of 32115 union entries)"),
             "fp64_flops_per_cell": head["fp64_flops_per_cell"],
             "radial_flops_per_cell": head["radial_flops_per_cell"],
             "radial_note": "low-precision radial flops: tensor-core (bf16, tf32) or FP32 CUDA-core (rf32)",
