@@ -74,17 +74,22 @@ typedef enum {
  * real by the unitary complex->real map), slices (c, q1), and the device
  * programs of the evaluation kernels.  gamma is the cross-section exponent of
  * B = u^gamma / (4 pi) (0 Maxwell molecules, 1 hard spheres, 0.5 VHS); it is
- * only recorded here (the core carries the physics).  Uses the current CUDA
- * device.  On success *out owns device memory until wef_destroy.
+ * only recorded here (the core carries the physics).  Host only: the device
+ * copies are made by the first wef_upload_core, on the device current then, and
+ * the operator is bound to that device until wef_destroy.
+ * Errors: WEF_EINVAL (out NULL, gamma outside [0, 2]), WEF_ESHAPE (Kmax or Lmax
+ * out of range), WEF_ENOMEM.
  */
 wef_status wef_create(int kmax, int lmax, double gamma, wef_op* out);
 
 /* Sizes of the operator: N = K*NQ per cell, number of channels N_T, Gaunt
- * nonzeros N_G, and the core length N_T*K^3 (doubles).  Any out pointer may be NULL. */
+ * nonzeros N_G, and the core length N_T*K^3 (doubles).  Any out pointer may be NULL.
+ * Errors: WEF_EINVAL (op NULL). */
 wef_status wef_sizes(wef_op op, int64_t* n_per_cell, int64_t* n_channels, int64_t* n_gaunt, int64_t* core_len);
 
 /* Copy the COO table of Table 1 order (q3 slowest, q1 fastest; 0-based
- * indices) into host arrays of length >= N_G.  Any array may be NULL. */
+ * indices) into host arrays of length >= N_G.  Any array may be NULL.
+ * Errors: WEF_EINVAL (op NULL). */
 wef_status wef_gaunt_coo(wef_op op, int32_t* q1, int32_t* q2, int32_t* q3, int32_t* c, double* g);
 
 /*
@@ -93,10 +98,15 @@ wef_status wef_gaunt_coo(wef_op op, int32_t* q1, int32_t* q2, int32_t* q3, int32
  * WEF_CORE_APPLY_NULLSPACE, the mass/momentum/energy slices (Sec. 4.4.2) and the
  * detailed-balance slice R^{(000)}_{k1,0,0} (Sec. 4.4.3) are zeroed first.
  * Synchronous.  The caller keeps R_host.  May be called again to replace the core.
+ * The first call binds the operator to the current device; later calls (and every
+ * evaluation) must be made with that device current.
+ * Errors: WEF_EINVAL (NULL argument, another device current), WEF_ESHAPE (len),
+ * WEF_ECUDA (device allocation or copy; the previous core is then released).
  */
 wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigned flags);
 
-/* Bytes of device workspace wef_evaluate needs for ncells cells (256-byte aligned use). */
+/* Bytes of device workspace wef_evaluate needs for ncells cells (256-byte aligned use).
+ * Errors: WEF_EINVAL (op or bytes NULL, ncells < 0, unknown precision). */
 wef_status wef_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int64_t* bytes);
 
 /*
@@ -108,6 +118,10 @@ wef_status wef_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int
  * The conservation projection (Sec. 4.4) writes exact zeros to the mass,
  * momentum and energy outputs (k=0,l=0), (k=0,l=1), (k=1,l=0) of every cell.
  * ncells == 0 is a no-op.
+ * Errors (checked before anything is queued): WEF_EINVAL (op or a buffer NULL, unknown
+ * precision, ncells < 0 or above 65535 * 32 * 1024, workspace unaligned or too small, a device other
+ * than the operator's current), WEF_ENOCORE (no core uploaded); WEF_ECUDA if a launch
+ * fails.
  */
 wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t ncells, wef_precision prec,
                         void* workspace, int64_t workspace_bytes, void* stream);
@@ -129,6 +143,12 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
  * Every operator must have a core uploaded (Kmax >= 1 for the tensor-core path) and
  * must outlive the plan.
  * Set-up allocations happen in wef_plan_create only.
+ * Errors: wef_plan_create - WEF_EINVAL (NULL argument, nops < 1, negative count, a
+ * precision other than those above), WEF_ENOCORE, WEF_ESHAPE (Kmax = 0 on the
+ * tensor-core path), WEF_ECUDA / WEF_ENOMEM (set-up); the launching calls - WEF_EINVAL
+ * (NULL plan or buffer, workspace unaligned or smaller than wef_plan_workspace_size),
+ * the errors of wef_evaluate for a shape's evaluation, WEF_ECUDA (launch, capture).  On
+ * an error the forked streams are still joined back to `stream`.
  */
 typedef struct wef_plan_s* wef_plan;
 wef_status wef_plan_create(const wef_op* ops, const int64_t* ncells, int nops, wef_precision prec, int granularity,
