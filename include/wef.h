@@ -240,6 +240,7 @@ wef_status wef_linearized_apply(wef_op op, const double* c0_dev, const double* d
  * machine).  pad_rad / pad_ang are the selective paddings of Appendix B (the
  * paper uses 10-20).  R_out: host array of length N_T*K^3.  Raw core: no
  * conservation zeroing is applied (pass WEF_CORE_APPLY_NULLSPACE to upload).
+ * Errors: WEF_EINVAL (NULL argument, padding outside [0, 200]), WEF_ESHAPE (len).
  */
 wef_status wef_core_build(wef_op op, int pad_rad, int pad_ang, double* R_out, int64_t len);
 
@@ -260,7 +261,7 @@ wef_status wef_core_build_device(wef_op op, int pad_rad, int pad_ang, double* R_
  * (radial contraction, padded MMA shapes, for the mixed precisions).  An FMA
  * counts as 2.  For WEF_RADIAL_FP32 the second output is the FP32 CUDA-core work of
  * the two radial contractions instead.  Derived from the operator's programs; any
- * out pointer may be NULL.
+ * out pointer may be NULL.  Errors: WEF_EINVAL (op NULL, unknown precision).
  */
 wef_status wef_flops(wef_op op, wef_precision prec, double* fp64_flops_per_cell, double* tc_flops_per_cell);
 
@@ -268,7 +269,8 @@ wef_status wef_flops(wef_op op, wef_precision prec, double* fp64_flops_per_cell,
  * wef_set_trace_events - tracing hook: when ev_start/ev_stop (cudaEvent_t) are
  * non-NULL, the next wef_evaluate calls record ev_start on the stream just before
  * the dominant (contraction) kernel and ev_stop just after it, so callers can
- * time that kernel alone.  Pass NULLs to switch tracing off.
+ * time that kernel alone.  Pass NULLs to switch tracing off.  The events stay the
+ * caller's and must outlive the calls that record them.  Errors: WEF_EINVAL (op NULL).
  */
 wef_status wef_set_trace_events(wef_op op, void* ev_start, void* ev_stop);
 
