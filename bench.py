@@ -18,6 +18,7 @@ Prints one JSON line (rank 0).  Under torchrun every rank evaluates its own batc
 the timed region are the only collectives.
 """
 import argparse
+import functools
 import json
 import os
 import statistics
@@ -98,6 +99,28 @@ def inputs(ncells, seed):
     return wi.two_maxwellians(KMAX, LMAX, ncells, seed=seed, pool=min(1024, ncells))
 
 
+@functools.lru_cache(maxsize=None)
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.machine()
+
+
 def cpu_baseline(sample_cells, sample_rows, seed=3, with_angular_first=False):
     """The oracle (dense FP64 CPU contraction) timed on a bounded sample of the workload:
     `sample_cells` cells and `sample_rows` of the N output rows, scaled to cells/s.  With
@@ -120,6 +143,7 @@ def cpu_baseline(sample_cells, sample_rows, seed=3, with_angular_first=False):
         "value": value,
         "unit": "cells/s",
         "cores": os.cpu_count(),
+        "cpu_model": cpu_model(),
         "kind": "oracle",
         "sample": f"{sample_cells} cells x {sample_rows} of {N} output rows (dense C slices), {dt:.1f} s; "
         f"numpy BLAS threads default (all {os.cpu_count()} host cores)",
@@ -141,7 +165,7 @@ def cpu_angular_first(sample_cells=32, seed=3):
     t0 = time.perf_counter()
     angular_first.evaluate(KMAX, LMAX, R, f, sl=sl)
     dt = time.perf_counter() - t0
-    return {"value": sample_cells / dt, "unit": "cells/s", "cores": 1,
+    return {"value": sample_cells / dt, "unit": "cells/s", "cores": 1, "cpu_model": cpu_model(),
             "kind": "angular-first numpy (Sec. 4.5.4)",
             "sample": f"{sample_cells} cells, {dt:.1f} s; numpy einsum without BLAS: one thread"}
 
