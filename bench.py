@@ -150,6 +150,7 @@ def cpu_baseline(sample_cells, sample_rows, seed=3, with_angular_first=False):
     }
     if with_angular_first:
         out["angular_first"] = cpu_angular_first()
+        out["angular_first_all_cores"] = cpu_angular_first_all_cores()
     return out
 
 
@@ -168,6 +169,44 @@ def cpu_angular_first(sample_cells=32, seed=3):
     return {"value": sample_cells / dt, "unit": "cells/s", "cores": 1, "cpu_model": cpu_model(),
             "kind": "angular-first numpy (Sec. 4.5.4)",
             "sample": f"{sample_cells} cells, {dt:.1f} s; numpy einsum without BLAS: one thread"}
+
+
+def _angular_first_worker(barrier, results, seed, cells):
+    """One process of cpu_angular_first_all_cores: set-up, wait for every process, evaluate."""
+    import wef_inputs as wi
+    from oracle import angular_first, gaunt
+
+    R = wi.random_core(len(gaunt.channels(LMAX)), KMAX, seed=11)
+    f = wi.two_maxwellians(KMAX, LMAX, cells, seed=seed)
+    sl = angular_first.slices(LMAX)
+    barrier.wait(timeout=600)
+    t0 = time.perf_counter()
+    angular_first.evaluate(KMAX, LMAX, R, f, sl=sl)
+    results.put((cells, t0, time.perf_counter()))
+
+
+def cpu_angular_first_all_cores(cells_per_process=24, seed=3, processes=None):
+    """The same numpy angular-first contraction on every host core (or on `processes`
+    cores): one spawned process per core, each on its own cells, released together by a
+    barrier; throughput = all cells over the wall time from the first start to the last
+    finish."""
+    import multiprocessing as mp
+
+    n = processes or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier, results = ctx.Barrier(n), ctx.Queue()
+    procs = [ctx.Process(target=_angular_first_worker, args=(barrier, results, seed + i, cells_per_process))
+             for i in range(n)]
+    for p in procs:
+        p.start()
+    got = [results.get(timeout=900) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    cells = sum(g[0] for g in got)
+    wall = max(g[2] for g in got) - min(g[1] for g in got)
+    return {"value": cells / wall, "unit": "cells/s", "cores": n, "cpu_model": cpu_model(),
+            "kind": "angular-first numpy (Sec. 4.5.4), one process per core",
+            "sample": f"{n} processes x {cells_per_process} cells, {wall:.1f} s wall from first start to last finish"}
 
 
 class ClockSampler:

@@ -18,3 +18,14 @@ def test_reference_arm_json_line():
     assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_angular_first_all_cores_figure():
+    """The all-cores CPU comparison figure (spawned processes, barrier, shared wall clock)
+    runs without a GPU and reports the processes it used."""
+    code = ("import json, bench; print(json.dumps(bench.cpu_angular_first_all_cores("
+            "cells_per_process=2, processes=2)))")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["cores"] == 2 and d["value"] > 0 and d["unit"] == "cells/s" and d["cpu_model"]
