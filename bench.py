@@ -737,7 +737,7 @@ def main():
             "traffic": TRAFFIC_BYTES.get(args.precision) if (ncells == NCELLS and KMAX == 12) else None,
             "traffic_note": ("DRAM bytes per launch (one-pass ncu capture at 16384 cells); algorithmic: FP32 tiles "
                              "in + FP64 Q out = 432 MB. Captured before q2 groups were paired by shared q3 "
-                             "(same kernel code, its program then had 32707 instead of 32115 union entries)"),
+                             "(same kernel code, its program then had 32707 instead of 31613 union entries)"),
             "fp64_flops_per_cell": head["fp64_flops_per_cell"],
             "radial_flops_per_cell": head["radial_flops_per_cell"],
             "radial_note": "low-precision radial flops: tensor-core (bf16, tf32) or FP32 CUDA-core (rf32)",

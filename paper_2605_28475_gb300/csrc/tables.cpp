@@ -317,17 +317,51 @@ std::string build_tables(int kmax, int lmax, Tables& t) {
           for (const Entry& e : sl[(size_t)sc * t.NQ + q1b + m]) byp[e.q2][e.q3].push_back({m, e.w});
         if (byp.empty()) continue;
         // q2 groups ordered so that each block of J shares as many q3 as possible: greedily,
-        // the first remaining group, then the J-1 groups sharing the most q3 with the block.
+        // the pair of remaining groups sharing the most q3 (ties: the lowest q2), then the
+        // J-2 groups sharing the most q3 with the block.
         std::vector<int> q2s;
         {
           std::vector<int> rest;
-          for (const auto& kv : byp) rest.push_back(kv.first);
+          std::map<int, std::vector<int>> q3of;  // q2 -> its q3, ascending
+          for (const auto& kv : byp) {
+            rest.push_back(kv.first);
+            for (const auto& kq : kv.second) q3of[kv.first].push_back(kq.first);
+          }
+          auto n_shared = [&](int a, int b) {
+            const std::vector<int>& x = q3of[a];
+            const std::vector<int>& y = q3of[b];
+            size_t n = 0;
+            for (size_t i = 0, k = 0; i < x.size() && k < y.size();) {
+              if (x[i] < y[k]) ++i;
+              else if (y[k] < x[i]) ++k;
+              else ++n, ++i, ++k;
+            }
+            return n;
+          };
           while (!rest.empty()) {
+            size_t sa = 0, sb = 0, best_pair = 0;
+            bool pair = false;
+            if (J > 1)
+              for (size_t i = 0; i < rest.size(); ++i)
+                for (size_t k = i + 1; k < rest.size(); ++k) {
+                  const size_t n = n_shared(rest[i], rest[k]);
+                  if (!pair || n > best_pair) {
+                    best_pair = n;
+                    sa = i;
+                    sb = k;
+                    pair = true;
+                  }
+                }
             std::set<int> uni;
-            for (const auto& kv : byp[rest.front()]) uni.insert(kv.first);
-            q2s.push_back(rest.front());
-            rest.erase(rest.begin());
-            for (int j = 1; j < J && !rest.empty(); ++j) {
+            auto take = [&](size_t i) {
+              for (const auto& kv : byp[rest[i]]) uni.insert(kv.first);
+              q2s.push_back(rest[i]);
+            };
+            take(sa);
+            if (pair) take(sb);
+            if (pair) rest.erase(rest.begin() + (long)sb);  // sb > sa
+            rest.erase(rest.begin() + (long)sa);
+            for (int j = pair ? 2 : 1; j < J && !rest.empty(); ++j) {
               size_t best = 0, best_shared = 0;
               for (size_t i = 0; i < rest.size(); ++i) {
                 size_t shared = 0;
