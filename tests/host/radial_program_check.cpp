@@ -3,12 +3,18 @@
 #include <cmath>
 #include <cstdio>
 #include <random>
+#include <utility>
 #include <vector>
 #include "../../paper_2605_28475_gb300/csrc/tables.hpp"
 using namespace wef;
 int main() {
   int bad = 0;
-  for (int L : {0, 1, 2, 3, 4, 6, 8, 12}) for (int km : {0, 1, 4, 8, 12, 16}) {
+  // every (Lmax, Kmax) of the grid, then the largest operators (tensor-memory placement)
+  std::vector<std::pair<int, int>> shapes;
+  for (int L : {0, 1, 2, 3, 4, 6, 8, 12}) for (int km : {0, 1, 4, 8, 12, 16}) shapes.push_back({L, km});
+  for (int L : {16, 20}) shapes.push_back({L, 16});
+  for (const auto& sh : shapes) {
+    const int L = sh.first, km = sh.second;
     Tables T; std::string e = build_tables(km, L, T); if (!e.empty()) { printf("err %s\n", e.c_str()); return 1; }
     const int K = T.K, NQ = T.NQ, NS = (int)T.sym_chan.size(), NT = (int)T.chans.size();
     std::mt19937_64 rng(km * 100 + L); std::normal_distribution<double> nd;
