@@ -127,23 +127,29 @@ def test_binding_rejects_mis_shaped_tensors():
         op.close()
 
 
-@pytest.mark.parametrize("km,lm", [(4, 4), (8, 8), (12, 12)])
-def test_radial_first_flop_counts_match_the_coo_table(km, lm):
-    """The per-cell work wef_flops reports for the radial-first path (the numerator of the
-    benchmark's roofline) against counts taken from the oracle's own COO table: the FP64
-    Gaunt reduction is 2K per symmetrised entry (q2 <= q3), the FP32 radial stages 2K^3 per
-    distinct (channel, q2) and 2K^2 per distinct (channel, q2, q3)."""
+@pytest.mark.parametrize("km,lm", [(4, 4), (8, 8), (12, 12), (12, 4)])
+def test_flop_counts_match_the_coo_table(km, lm):
+    """The per-cell work wef_flops reports (the numerator of the benchmark's roofline) against
+    counts taken from the oracle's own COO table.  Radial-first: the FP64 Gaunt reduction is
+    2K per symmetrised entry (q2 <= q3), the FP32 radial stages 2K^3 per distinct
+    (channel, q2) and 2K^2 per distinct (channel, q2, q3).  Plain FP64 angular-first: 2K^2
+    per rank-1 group (distinct channel, q1, q2), 2K per symmetrised entry and 2K^3 per
+    symmetrised slice (distinct channel, q1)."""
     q1, q2, q3, c, g = ogaunt.coo(lm)
     sym = q2 <= q3
     lof = lambda q: np.floor(np.sqrt(q + 0.5)).astype(int)  # noqa: E731
     l1, l2, l3 = lof(q1[sym]), lof(q2[sym]), lof(q3[sym])
     groups = {(a, b, d, e) for a, b, d, e in zip(l1, l2, l3, q2[sym])}
     pairs = {(a, b, d, e, f) for a, b, d, e, f in zip(l1, l2, l3, q2[sym], q3[sym])}
-    K = km + 1
+    rank1 = {(a, b, d, e, f) for a, b, d, e, f in zip(l1, l2, l3, q1[sym], q2[sym])}
+    slices = {(a, b, d, e) for a, b, d, e in zip(l1, l2, l3, q1[sym])}
+    K, E = km + 1, int(sym.sum())
     h = W.wef_create(km, lm, 1.0)
     try:
         fp64, fp32 = W.wef_flops(h, W.WEF_RADIAL_FP32)
+        plain, _ = W.wef_flops(h, W.WEF_FP64)
     finally:
         W.wef_destroy(h)
-    assert fp64 == 2 * K * int(sym.sum())
+    assert fp64 == 2 * K * E
     assert fp32 == 2 * K**3 * len(groups) + 2 * K**2 * len(pairs)
+    assert plain == 2 * K**2 * len(rank1) + 2 * K * E + 2 * K**3 * len(slices)
