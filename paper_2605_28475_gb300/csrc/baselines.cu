@@ -135,30 +135,32 @@ extern "C" {
 
 wef_status wef_naive_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t ncells, void* workspace,
                               int64_t ws_bytes, void* stream) {
-  if (!op || ncells < 0) return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: bad argument");
-  if (ncells == 0) return WEF_OK;
-  if (!f_dev || !q_dev || !workspace) return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: NULL buffer");
-  if (!op->has_core) return wef::set_error(WEF_ENOCORE, "wef_naive_evaluate: no core uploaded");
-  if (((uintptr_t)workspace & 255) != 0)
-    return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: workspace not 256-byte aligned");
-  int64_t need = 0;
-  wef_workspace_size(op, ncells, WEF_FP64, &need);
-  if (ws_bytes < need) return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: workspace too small");
-  if (ncells > (int64_t)65535 * 32 * 1024) return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: ncells too large");
-  cudaError_t e = ensure_entries(op);
-  if (e != cudaSuccess) return wef::set_error(WEF_ECUDA, std::string("wef_naive_evaluate: ") + cudaGetErrorString(e));
-  const int K = op->T.K, NQ = op->T.NQ;
-  cudaStream_t s = (cudaStream_t)stream;
-  double* ftile = (double*)workspace;
-  e = wef::launch_tile_f(f_dev, ftile, ncells, K, NQ, s);
-  if (e == cudaSuccess) {
-    const int64_t ntiles = (ncells + 31) / 32;
-    naive_coo_kernel<<<dim3((unsigned)ntiles, (unsigned)NQ), 32 * K, 0, s>>>(
-        ftile, q_dev, ncells, K, NQ, (const int4*)op->b_ent, op->b_w, op->b_off, op->d_R64);
-    e = cudaGetLastError();
-  }
-  if (e != cudaSuccess) return wef::set_error(WEF_ECUDA, std::string("wef_naive_evaluate: ") + cudaGetErrorString(e));
-  return WEF_OK;
+  return wef::guarded("wef_naive_evaluate", [&]() -> wef_status {
+    if (!op || ncells < 0) return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: bad argument");
+    if (ncells == 0) return WEF_OK;
+    if (!f_dev || !q_dev || !workspace) return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: NULL buffer");
+    if (!op->has_core) return wef::set_error(WEF_ENOCORE, "wef_naive_evaluate: no core uploaded");
+    if (((uintptr_t)workspace & 255) != 0)
+      return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: workspace not 256-byte aligned");
+    int64_t need = 0;
+    wef_workspace_size(op, ncells, WEF_FP64, &need);
+    if (ws_bytes < need) return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: workspace too small");
+    if (ncells > (int64_t)65535 * 32 * 1024) return wef::set_error(WEF_EINVAL, "wef_naive_evaluate: ncells too large");
+    cudaError_t e = ensure_entries(op);
+    if (e != cudaSuccess) return wef::set_error(WEF_ECUDA, std::string("wef_naive_evaluate: ") + cudaGetErrorString(e));
+    const int K = op->T.K, NQ = op->T.NQ;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* ftile = (double*)workspace;
+    e = wef::launch_tile_f(f_dev, ftile, ncells, K, NQ, s);
+    if (e == cudaSuccess) {
+      const int64_t ntiles = (ncells + 31) / 32;
+      naive_coo_kernel<<<dim3((unsigned)ntiles, (unsigned)NQ), 32 * K, 0, s>>>(
+          ftile, q_dev, ncells, K, NQ, (const int4*)op->b_ent, op->b_w, op->b_off, op->d_R64);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return wef::set_error(WEF_ECUDA, std::string("wef_naive_evaluate: ") + cudaGetErrorString(e));
+    return WEF_OK;
+  });
 }
 
 wef_status wef_dense_tensor_size(wef_op op, int64_t* bytes) {
@@ -169,21 +171,23 @@ wef_status wef_dense_tensor_size(wef_op op, int64_t* bytes) {
 }
 
 wef_status wef_dense_assemble(wef_op op, double* C_dev, int64_t bytes, void* stream) {
-  if (!op || !C_dev) return wef::set_error(WEF_EINVAL, "wef_dense_assemble: bad argument");
-  if (!op->has_core) return wef::set_error(WEF_ENOCORE, "wef_dense_assemble: no core uploaded");
-  int64_t need = 0;
-  wef_dense_tensor_size(op, &need);
-  if (bytes < need) return wef::set_error(WEF_EINVAL, "wef_dense_assemble: buffer too small");
-  cudaError_t e = ensure_entries(op);
-  cudaStream_t s = (cudaStream_t)stream;
-  if (e == cudaSuccess) e = cudaMemsetAsync(C_dev, 0, (size_t)need, s);
-  if (e == cudaSuccess && op->b_nent > 0) {
-    dense_assemble_kernel<<<op->sms * 8, 256, 0, s>>>(C_dev, op->T.K, op->T.NQ, op->b_nent, (const int4*)op->b_ent,
-                                                       op->b_w, op->b_off, op->d_R64);
-    e = cudaGetLastError();
-  }
-  if (e != cudaSuccess) return wef::set_error(WEF_ECUDA, std::string("wef_dense_assemble: ") + cudaGetErrorString(e));
-  return WEF_OK;
+  return wef::guarded("wef_dense_assemble", [&]() -> wef_status {
+    if (!op || !C_dev) return wef::set_error(WEF_EINVAL, "wef_dense_assemble: bad argument");
+    if (!op->has_core) return wef::set_error(WEF_ENOCORE, "wef_dense_assemble: no core uploaded");
+    int64_t need = 0;
+    wef_dense_tensor_size(op, &need);
+    if (bytes < need) return wef::set_error(WEF_EINVAL, "wef_dense_assemble: buffer too small");
+    cudaError_t e = ensure_entries(op);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (e == cudaSuccess) e = cudaMemsetAsync(C_dev, 0, (size_t)need, s);
+    if (e == cudaSuccess && op->b_nent > 0) {
+      dense_assemble_kernel<<<op->sms * 8, 256, 0, s>>>(C_dev, op->T.K, op->T.NQ, op->b_nent, (const int4*)op->b_ent,
+                                                         op->b_w, op->b_off, op->d_R64);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return wef::set_error(WEF_ECUDA, std::string("wef_dense_assemble: ") + cudaGetErrorString(e));
+    return WEF_OK;
+  });
 }
 
 wef_status wef_dense_workspace_size(wef_op op, int64_t ncells, int64_t* bytes) {

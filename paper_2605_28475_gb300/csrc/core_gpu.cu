@@ -341,85 +341,87 @@ cudaError_t to_dev(T** dst, const std::vector<T>& v) {
 }  // namespace
 
 extern "C" wef_status wef_core_build_device(wef_op op, int pad_rad, int pad_ang, double* R_out, int64_t len) {
-  if (!op || !R_out) return wef::set_error(WEF_EINVAL, "wef_core_build_device: NULL argument");
-  const int K = op->T.K, L1 = op->T.lmax + 1;
-  if (len != (int64_t)op->T.chans.size() * K * K * K)
-    return wef::set_error(WEF_ESHAPE, "wef_core_build_device: len must be N_T*K^3");
-  if (pad_rad < 0 || pad_ang < 0 || pad_rad > 200 || pad_ang > 200)
-    return wef::set_error(WEF_EINVAL, "wef_core_build_device: bad padding");
-  if (K > kMaxK || L1 > kMaxL1) return wef::set_error(WEF_ESHAPE, "wef_core_build_device: Kmax <= 16, Lmax <= 20");
-  wef::CoreQuad Q;
-  std::string err = wef::core_quadrature(op->T, op->gamma, pad_rad, pad_ang, Q);
-  if (!err.empty()) return wef::set_error(WEF_EINVAL, "wef_core_build_device: " + err);
-  Geo g;
-  g.K = K;
-  g.L1 = L1;
-  g.Nx1 = (int)Q.x1.size();
-  g.Nh1 = (int)Q.h1.size();
-  g.Ny2 = (int)Q.y2.size();
-  g.Nh2 = (int)Q.h2.size();
-  g.nft = (int)Q.ftx.size();
-  g.DA = 1 + K * L1 + 2 * L1 * L1;
-  g.DR = 2 * K * L1;
-  g.na_zh = (int64_t)g.Nx1 * g.Nh1 + (int64_t)g.Ny2 * g.Nh2;
-  g.nr_zh = (int64_t)g.Nx1 + (int64_t)g.Ny2 * g.Nh2;
-  g.gamma = Q.gamma;
-  g.pref = Q.pref;
-  const int Nz = (int)Q.zz.size(), NT = Q.NT;
-  // z nodes per chunk: point tables of about 1 GB at most
-  const int64_t bytes_z = 2 * (g.na_zh * g.DA + g.nr_zh * g.DR) * (int64_t)sizeof(double);
-  const int zc = (int)std::max<int64_t>(1, std::min<int64_t>(Nz, (int64_t)(1LL << 30) / bytes_z));
-  std::vector<int32_t> chv;
-  for (int c = 0; c < NT; ++c) {
-    const wef::Channel& h = Q.ch[c];
-    chv.insert(chv.end(), {h.l1, h.l2, h.l3, Q.Ghat_off[c]});
-  }
-  std::vector<double> fscale(NT);
-  for (int c = 0; c < NT; ++c) fscale[c] = 8.0 * M_PI * M_PI / Q.S[c];
-  std::vector<double*> bufs;
-  auto dv = [&](const std::vector<double>& v, const double** p) {
-    double* q = nullptr;
-    cudaError_t e = to_dev(&q, v);
-    bufs.push_back(q);
-    *p = q;
-    return e;
-  };
-  Dev d{};
-  cudaError_t e = cudaSuccess;
-  const std::vector<const std::vector<double>*> src = {&Q.zz, &Q.wz, &Q.x1, &Q.wx1, &Q.h1, &Q.wh1, &Q.y2,
-                                                        &Q.wy2, &Q.h2, &Q.wh2, &Q.ftx, &Q.ftw, &Q.Nkl, &Q.ylm_norm};
-  const double** dst[] = {&d.zz, &d.wz, &d.x1, &d.wx1, &d.h1, &d.wh1, &d.y2,
-                          &d.wy2, &d.h2, &d.wh2, &d.ftx, &d.ftw, &d.Nkl, &d.ylm_norm};
-  for (size_t i = 0; i < src.size() && e == cudaSuccess; ++i) e = dv(*src[i], dst[i]);
-  ChanDev cd{};
-  int32_t* dch = nullptr;
-  double *A = nullptr, *Rr = nullptr, *Rd = nullptr;
-  if (e == cudaSuccess) e = to_dev(&dch, chv);
-  cd.ch = (const int4*)dch;
-  if (e == cudaSuccess) e = dv(Q.Ghat, &cd.Ghat);
-  if (e == cudaSuccess) e = dv(Q.s2, &cd.s2);
-  if (e == cudaSuccess) e = dv(fscale, &cd.fscale);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&A, (size_t)zc * 2 * g.na_zh * g.DA * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&Rr, (size_t)zc * 2 * g.nr_zh * g.DR * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&Rd, (size_t)len * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemset(Rd, 0, (size_t)len * sizeof(double));
-  const int threads2 = (K * K + 31) / 32 * 32;
-  for (int iz0 = 0; iz0 < Nz && e == cudaSuccess; iz0 += zc) {
-    g.nz_chunk = std::min(zc, Nz - iz0);
-    const int64_t na = (int64_t)g.nz_chunk * 2 * g.na_zh, nr = (int64_t)g.nz_chunk * 2 * g.nr_zh;
-    g.na = na;
-    g.nr = nr;
-    angular_points_kernel<<<(unsigned)((na * 32 + 255) / 256), 256>>>(g, d, iz0, A);
-    radial_points_kernel<<<(unsigned)((nr * 32 + 255) / 256), 256>>>(g, d, iz0, Rr);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = launch_contract(K, NT, threads2, g, d, cd, A, Rr, Rd);
-  }
-  if (e == cudaSuccess) e = cudaMemcpy(R_out, Rd, (size_t)len * sizeof(double), cudaMemcpyDeviceToHost);
-  for (double* p : bufs) cudaFree(p);
-  cudaFree(dch);
-  cudaFree(A);
-  cudaFree(Rr);
-  cudaFree(Rd);
-  if (e != cudaSuccess) return wef::set_error(WEF_ECUDA, std::string("wef_core_build_device: ") + cudaGetErrorString(e));
-  return WEF_OK;
+  return wef::guarded("wef_core_build_device", [&]() -> wef_status {
+    if (!op || !R_out) return wef::set_error(WEF_EINVAL, "wef_core_build_device: NULL argument");
+    const int K = op->T.K, L1 = op->T.lmax + 1;
+    if (len != (int64_t)op->T.chans.size() * K * K * K)
+      return wef::set_error(WEF_ESHAPE, "wef_core_build_device: len must be N_T*K^3");
+    if (pad_rad < 0 || pad_ang < 0 || pad_rad > 200 || pad_ang > 200)
+      return wef::set_error(WEF_EINVAL, "wef_core_build_device: bad padding");
+    if (K > kMaxK || L1 > kMaxL1) return wef::set_error(WEF_ESHAPE, "wef_core_build_device: Kmax <= 16, Lmax <= 20");
+    wef::CoreQuad Q;
+    std::string err = wef::core_quadrature(op->T, op->gamma, pad_rad, pad_ang, Q);
+    if (!err.empty()) return wef::set_error(WEF_EINVAL, "wef_core_build_device: " + err);
+    Geo g;
+    g.K = K;
+    g.L1 = L1;
+    g.Nx1 = (int)Q.x1.size();
+    g.Nh1 = (int)Q.h1.size();
+    g.Ny2 = (int)Q.y2.size();
+    g.Nh2 = (int)Q.h2.size();
+    g.nft = (int)Q.ftx.size();
+    g.DA = 1 + K * L1 + 2 * L1 * L1;
+    g.DR = 2 * K * L1;
+    g.na_zh = (int64_t)g.Nx1 * g.Nh1 + (int64_t)g.Ny2 * g.Nh2;
+    g.nr_zh = (int64_t)g.Nx1 + (int64_t)g.Ny2 * g.Nh2;
+    g.gamma = Q.gamma;
+    g.pref = Q.pref;
+    const int Nz = (int)Q.zz.size(), NT = Q.NT;
+    // z nodes per chunk: point tables of about 1 GB at most
+    const int64_t bytes_z = 2 * (g.na_zh * g.DA + g.nr_zh * g.DR) * (int64_t)sizeof(double);
+    const int zc = (int)std::max<int64_t>(1, std::min<int64_t>(Nz, (int64_t)(1LL << 30) / bytes_z));
+    std::vector<int32_t> chv;
+    for (int c = 0; c < NT; ++c) {
+      const wef::Channel& h = Q.ch[c];
+      chv.insert(chv.end(), {h.l1, h.l2, h.l3, Q.Ghat_off[c]});
+    }
+    std::vector<double> fscale(NT);
+    for (int c = 0; c < NT; ++c) fscale[c] = 8.0 * M_PI * M_PI / Q.S[c];
+    std::vector<double*> bufs;
+    auto dv = [&](const std::vector<double>& v, const double** p) {
+      double* q = nullptr;
+      cudaError_t e = to_dev(&q, v);
+      bufs.push_back(q);
+      *p = q;
+      return e;
+    };
+    Dev d{};
+    cudaError_t e = cudaSuccess;
+    const std::vector<const std::vector<double>*> src = {&Q.zz, &Q.wz, &Q.x1, &Q.wx1, &Q.h1, &Q.wh1, &Q.y2,
+                                                          &Q.wy2, &Q.h2, &Q.wh2, &Q.ftx, &Q.ftw, &Q.Nkl, &Q.ylm_norm};
+    const double** dst[] = {&d.zz, &d.wz, &d.x1, &d.wx1, &d.h1, &d.wh1, &d.y2,
+                            &d.wy2, &d.h2, &d.wh2, &d.ftx, &d.ftw, &d.Nkl, &d.ylm_norm};
+    for (size_t i = 0; i < src.size() && e == cudaSuccess; ++i) e = dv(*src[i], dst[i]);
+    ChanDev cd{};
+    int32_t* dch = nullptr;
+    double *A = nullptr, *Rr = nullptr, *Rd = nullptr;
+    if (e == cudaSuccess) e = to_dev(&dch, chv);
+    cd.ch = (const int4*)dch;
+    if (e == cudaSuccess) e = dv(Q.Ghat, &cd.Ghat);
+    if (e == cudaSuccess) e = dv(Q.s2, &cd.s2);
+    if (e == cudaSuccess) e = dv(fscale, &cd.fscale);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&A, (size_t)zc * 2 * g.na_zh * g.DA * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Rr, (size_t)zc * 2 * g.nr_zh * g.DR * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Rd, (size_t)len * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(Rd, 0, (size_t)len * sizeof(double));
+    const int threads2 = (K * K + 31) / 32 * 32;
+    for (int iz0 = 0; iz0 < Nz && e == cudaSuccess; iz0 += zc) {
+      g.nz_chunk = std::min(zc, Nz - iz0);
+      const int64_t na = (int64_t)g.nz_chunk * 2 * g.na_zh, nr = (int64_t)g.nz_chunk * 2 * g.nr_zh;
+      g.na = na;
+      g.nr = nr;
+      angular_points_kernel<<<(unsigned)((na * 32 + 255) / 256), 256>>>(g, d, iz0, A);
+      radial_points_kernel<<<(unsigned)((nr * 32 + 255) / 256), 256>>>(g, d, iz0, Rr);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = launch_contract(K, NT, threads2, g, d, cd, A, Rr, Rd);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(R_out, Rd, (size_t)len * sizeof(double), cudaMemcpyDeviceToHost);
+    for (double* p : bufs) cudaFree(p);
+    cudaFree(dch);
+    cudaFree(A);
+    cudaFree(Rr);
+    cudaFree(Rd);
+    if (e != cudaSuccess) return wef::set_error(WEF_ECUDA, std::string("wef_core_build_device: ") + cudaGetErrorString(e));
+    return WEF_OK;
+  });
 }

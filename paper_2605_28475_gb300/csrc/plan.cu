@@ -11,6 +11,7 @@
 #include <cstring>
 #include <fstream>
 #include <map>
+#include <memory>
 #include <new>
 #include <sstream>
 #include <string>
@@ -240,139 +241,128 @@ extern "C" {
 
 wef_status wef_plan_create(const wef_op* ops, const int64_t* ncells, int nops, wef_precision prec, int granularity,
                            wef_plan* out) {
-  if (!out || !ops || !ncells || nops <= 0) return set_error(WEF_EINVAL, "wef_plan_create: bad argument");
-  *out = nullptr;
-  const bool rf = prec == WEF_RADIAL_FP32;
-  if (prec != WEF_MIXED_TF32 && prec != WEF_MIXED_BF16 && !rf)
-    return set_error(WEF_EINVAL, "wef_plan_create: ragged plans run the tensor-core (BF16, TF32) or radial-first path");
-  wef_plan_s* P = new (std::nothrow) wef_plan_s();
-  if (!P) return set_error(WEF_ENOMEM, "wef_plan_create: host allocation failed");
-  P->prec = prec;
-  std::ostringstream key;
-  key << (rf ? "rf32" : prec == WEF_MIXED_TF32 ? "tf32" : "bf16");
-  int64_t tile0 = 0, fo = 0, wo = 0;
-  for (int i = 0; i < nops; ++i) {
-    wef_op op = ops[i];
-    if (!op || ncells[i] < 0) {
-      delete P;
-      return set_error(WEF_EINVAL, "wef_plan_create: NULL operator or negative count");
+  return wef::guarded("wef_plan_create", [&]() -> wef_status {
+    if (!out || !ops || !ncells || nops <= 0) return set_error(WEF_EINVAL, "wef_plan_create: bad argument");
+    *out = nullptr;
+    const bool rf = prec == WEF_RADIAL_FP32;
+    if (prec != WEF_MIXED_TF32 && prec != WEF_MIXED_BF16 && !rf)
+      return set_error(WEF_EINVAL, "wef_plan_create: ragged plans run the tensor-core (BF16, TF32) or radial-first path");
+    wef_plan_s* P = new (std::nothrow) wef_plan_s();
+    if (!P) return set_error(WEF_ENOMEM, "wef_plan_create: host allocation failed");
+    // owns the plan until it is handed out: every early return (and any exception)
+    // releases its device resources
+    std::unique_ptr<wef_plan_s, void (*)(wef_plan_s*)> hold(P, [](wef_plan_s* x) {
+      x->release();
+      delete x;
+    });
+    P->prec = prec;
+    std::ostringstream key;
+    key << (rf ? "rf32" : prec == WEF_MIXED_TF32 ? "tf32" : "bf16");
+    int64_t tile0 = 0, fo = 0, wo = 0;
+    for (int i = 0; i < nops; ++i) {
+      wef_op op = ops[i];
+      if (!op || ncells[i] < 0) {
+        return set_error(WEF_EINVAL, "wef_plan_create: NULL operator or negative count");
+      }
+      if (!op->has_core || !op->d_Bbf16) {
+        return set_error(WEF_ENOCORE, "wef_plan_create: every operator needs an uploaded core");
+      }
+      if (op->T.K < 2 && !rf) {
+        return set_error(WEF_ESHAPE, "wef_plan_create: the tensor-core path needs Kmax >= 1");
+      }
+      RaggedShape S{};
+      S.K = op->T.K;
+      S.NQ = op->T.NQ;
+      S.ncells = ncells[i];
+      S.tile0 = tile0;
+      S.f_off = fo;
+      S.q_off = fo;
+      S.ftile_off = wo;
+      S.prog = op->dp[1].prog;
+      S.groups = (const int4*)op->dp[1].groups;
+      S.gw = (const double2*)op->dp[1].gw;
+      S.task_off = op->dp[1].off;
+      S.Bbf16 = op->d_Bbf16;
+      S.Btf32 = op->d_Btf32;
+      const int64_t nt = (ncells[i] + 31) / 32;
+      const int64_t N = (int64_t)S.K * S.NQ;
+      tile0 += nt;
+      fo += ncells[i] * N;
+      wo += nt * 32 * N;
+      P->ops.push_back(op);
+      P->ncells.push_back(ncells[i]);
+      P->shapes.push_back(S);
+      P->max_k = std::max(P->max_k, S.K);
+      P->max_n = std::max(P->max_n, (int)N);
+      P->total_cells += ncells[i];
+      key << "_" << (S.K - 1) << "x" << op->T.lmax << "x" << ncells[i];
+      P->nsm = op->sms;
     }
-    if (!op->has_core || !op->d_Bbf16) {
-      delete P;
-      return set_error(WEF_ENOCORE, "wef_plan_create: every operator needs an uploaded core");
+    P->total_tiles = tile0;
+    P->ws_bytes = wo * (int64_t)sizeof(double);
+    if (rf) {
+      // one radial-first workspace per shape (they run concurrently), 256-byte aligned
+      int64_t off = 0;
+      std::vector<double> cost;
+      for (size_t i = 0; i < P->ops.size(); ++i) {
+        int64_t b = 0;
+        wef_workspace_size(P->ops[i], P->ncells[i], WEF_RADIAL_FP32, &b);
+        b = std::max<int64_t>((b + 255) / 256 * 256, 256);
+        P->rf_ws_off.push_back(off);
+        P->rf_ws_len.push_back(b);
+        off += b;
+        cost.push_back((double)P->ncells[i] * (P->ops[i]->T.rprog.fp64_flops + P->ops[i]->T.rprog.fp32_flops / 64.0));
+        P->rf_order.push_back((int)i);
+      }
+      std::stable_sort(P->rf_order.begin(), P->rf_order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+      P->ws_bytes = off;
     }
-    if (op->T.K < 2 && !rf) {
-      delete P;
-      return set_error(WEF_ESHAPE, "wef_plan_create: the tensor-core path needs Kmax >= 1");
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) key << "_" << prop.name;
+    P->key = key.str();
+    for (auto& ch : P->key)
+      if (ch == ' ') ch = '-';
+    cudaError_t e = cudaMalloc((void**)&P->d_shapes, P->shapes.size() * sizeof(RaggedShape));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(P->d_shapes, P->shapes.data(), P->shapes.size() * sizeof(RaggedShape), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&P->d_queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&P->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(P->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    for (int i = 0; rf && i < wef_plan_s::kMaxFork && e == cudaSuccess; ++i)
+      e = cudaStreamCreateWithFlags(&P->fork[i], cudaStreamNonBlocking);
+    for (int i = 0; rf && i <= wef_plan_s::kMaxFork && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&P->fork_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("wef_plan_create: ") + cudaGetErrorString(e));
+    if (rf) {
+      // the tuned quantity is the number of concurrent shape streams
+      int nf = granularity > 0 ? granularity : cache_lookup(P->key);
+      P->nfork = nf > 0 ? std::min(nf, (int)wef_plan_s::kMaxFork) : 4;
+      P->granularity = P->nfork;
+      // kernel attributes of every shape now, outside any later stream capture
+      for (size_t i = 0; i < P->ops.size() && e == cudaSuccess; ++i)
+        e = prepare_rf(P->ops[i]->T.K, P->ops[i]->T.rprog.n1max);
+      if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("wef_plan_create: ") + cudaGetErrorString(e));
+      *out = hold.release();
+      return WEF_OK;
     }
-    RaggedShape S{};
-    S.K = op->T.K;
-    S.NQ = op->T.NQ;
-    S.ncells = ncells[i];
-    S.tile0 = tile0;
-    S.f_off = fo;
-    S.q_off = fo;
-    S.ftile_off = wo;
-    S.prog = op->dp[1].prog;
-    S.groups = (const int4*)op->dp[1].groups;
-    S.gw = (const double2*)op->dp[1].gw;
-    S.task_off = op->dp[1].off;
-    S.Bbf16 = op->d_Bbf16;
-    S.Btf32 = op->d_Btf32;
-    const int64_t nt = (ncells[i] + 31) / 32;
-    const int64_t N = (int64_t)S.K * S.NQ;
-    tile0 += nt;
-    fo += ncells[i] * N;
-    wo += nt * 32 * N;
-    P->ops.push_back(op);
-    P->ncells.push_back(ncells[i]);
-    P->shapes.push_back(S);
-    P->max_k = std::max(P->max_k, S.K);
-    P->max_n = std::max(P->max_n, (int)N);
-    P->total_cells += ncells[i];
-    key << "_" << (S.K - 1) << "x" << op->T.lmax << "x" << ncells[i];
-    P->nsm = op->sms;
-  }
-  P->total_tiles = tile0;
-  P->ws_bytes = wo * (int64_t)sizeof(double);
-  if (rf) {
-    // one radial-first workspace per shape (they run concurrently), 256-byte aligned
-    int64_t off = 0;
-    std::vector<double> cost;
-    for (size_t i = 0; i < P->ops.size(); ++i) {
-      int64_t b = 0;
-      wef_workspace_size(P->ops[i], P->ncells[i], WEF_RADIAL_FP32, &b);
-      b = std::max<int64_t>((b + 255) / 256 * 256, 256);
-      P->rf_ws_off.push_back(off);
-      P->rf_ws_len.push_back(b);
-      off += b;
-      cost.push_back((double)P->ncells[i] * (P->ops[i]->T.rprog.fp64_flops + P->ops[i]->T.rprog.fp32_flops / 64.0));
-      P->rf_order.push_back((int)i);
+    // granularity: explicit, cached from an earlier autotune, or enough items for ~8 per SM
+    int g = granularity;
+    if (g <= 0) g = cache_lookup(P->key);
+    if (g <= 0) {
+      g = 1;
+      while (g < 64 && (int64_t)P->total_tiles * g < 8LL * P->nsm) g *= 2;
     }
-    std::stable_sort(P->rf_order.begin(), P->rf_order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    P->ws_bytes = off;
-  }
-  cudaDeviceProp prop;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) key << "_" << prop.name;
-  P->key = key.str();
-  for (auto& ch : P->key)
-    if (ch == ' ') ch = '-';
-  cudaError_t e = cudaMalloc((void**)&P->d_shapes, P->shapes.size() * sizeof(RaggedShape));
-  if (e == cudaSuccess)
-    e = cudaMemcpy(P->d_shapes, P->shapes.data(), P->shapes.size() * sizeof(RaggedShape), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&P->d_queue, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&P->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(P->d_status, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
-  for (int i = 0; rf && i < wef_plan_s::kMaxFork && e == cudaSuccess; ++i)
-    e = cudaStreamCreateWithFlags(&P->fork[i], cudaStreamNonBlocking);
-  for (int i = 0; rf && i <= wef_plan_s::kMaxFork && e == cudaSuccess; ++i)
-    e = cudaEventCreateWithFlags(&P->fork_ev[i], cudaEventDisableTiming);
-  if (e != cudaSuccess) {
-    P->release();
-    delete P;
-    return set_error(WEF_ECUDA, std::string("wef_plan_create: ") + cudaGetErrorString(e));
-  }
-  if (rf) {
-    // the tuned quantity is the number of concurrent shape streams
-    int nf = granularity > 0 ? granularity : cache_lookup(P->key);
-    P->nfork = nf > 0 ? std::min(nf, (int)wef_plan_s::kMaxFork) : 4;
-    P->granularity = P->nfork;
-    // kernel attributes of every shape now, outside any later stream capture
-    for (size_t i = 0; i < P->ops.size() && e == cudaSuccess; ++i)
-      e = prepare_rf(P->ops[i]->T.K, P->ops[i]->T.rprog.n1max);
-    if (e != cudaSuccess) {
-      P->release();
-      delete P;
-      return set_error(WEF_ECUDA, std::string("wef_plan_create: ") + cudaGetErrorString(e));
-    }
-    *out = P;
+    wef_status st = set_items(P, g);
+    if (st != WEF_OK) return st;
+    // kernel attributes now, outside any later stream capture
+    e = prepare_ragged_tc();
+    if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("wef_plan_create: ") + cudaGetErrorString(e));
+    *out = hold.release();
     return WEF_OK;
-  }
-  // granularity: explicit, cached from an earlier autotune, or enough items for ~8 per SM
-  int g = granularity;
-  if (g <= 0) g = cache_lookup(P->key);
-  if (g <= 0) {
-    g = 1;
-    while (g < 64 && (int64_t)P->total_tiles * g < 8LL * P->nsm) g *= 2;
-  }
-  wef_status st = set_items(P, g);
-  if (st != WEF_OK) {
-    P->release();
-    delete P;
-    return st;
-  }
-  // kernel attributes now, outside any later stream capture
-  e = prepare_ragged_tc();
-  if (e != cudaSuccess) {
-    P->release();
-    delete P;
-    return set_error(WEF_ECUDA, std::string("wef_plan_create: ") + cudaGetErrorString(e));
-  }
-  *out = P;
-  return WEF_OK;
+  });
 }
 
 wef_status wef_plan_workspace_size(wef_plan plan, int64_t* bytes) {
@@ -383,108 +373,114 @@ wef_status wef_plan_workspace_size(wef_plan plan, int64_t* bytes) {
 
 wef_status wef_plan_execute(wef_plan plan, const double* f_dev, double* q_dev, void* workspace, int64_t ws_bytes,
                             void* stream) {
-  if (!plan) return set_error(WEF_EINVAL, "wef_plan_execute: plan is NULL");
-  wef_status st = check_buffers(plan, f_dev, q_dev, workspace, ws_bytes);
-  if (st != WEF_OK) return st;
-  return plan_launch(plan, f_dev, q_dev, workspace, (cudaStream_t)stream);
+  return wef::guarded("wef_plan_execute", [&]() -> wef_status {
+    if (!plan) return set_error(WEF_EINVAL, "wef_plan_execute: plan is NULL");
+    wef_status st = check_buffers(plan, f_dev, q_dev, workspace, ws_bytes);
+    if (st != WEF_OK) return st;
+    return plan_launch(plan, f_dev, q_dev, workspace, (cudaStream_t)stream);
+  });
 }
 
 wef_status wef_plan_graph_launch(wef_plan plan, const double* f_dev, double* q_dev, void* workspace, int64_t ws_bytes,
                                  void* stream) {
-  if (!plan) return set_error(WEF_EINVAL, "wef_plan_graph_launch: plan is NULL");
-  wef_status st = check_buffers(plan, f_dev, q_dev, workspace, ws_bytes);
-  if (st != WEF_OK) return st;
-  if (plan->total_cells == 0) return WEF_OK;
-  if (plan->gexec && (plan->g_f != f_dev || plan->g_q != q_dev || plan->g_ws != workspace)) {
-    cudaGraphExecDestroy(plan->gexec);
-    plan->gexec = nullptr;
-  }
-  if (!plan->gexec) {
-    // first call (or new buffers): capture the two launches on the plan's own stream
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    wef_status ls = plan_launch(plan, f_dev, q_dev, workspace, plan->cap_stream);
-    e = cudaStreamEndCapture(plan->cap_stream, &graph);
-    if (ls != WEF_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return ls;
+  return wef::guarded("wef_plan_graph_launch", [&]() -> wef_status {
+    if (!plan) return set_error(WEF_EINVAL, "wef_plan_graph_launch: plan is NULL");
+    wef_status st = check_buffers(plan, f_dev, q_dev, workspace, ws_bytes);
+    if (st != WEF_OK) return st;
+    if (plan->total_cells == 0) return WEF_OK;
+    if (plan->gexec && (plan->g_f != f_dev || plan->g_q != q_dev || plan->g_ws != workspace)) {
+      cudaGraphExecDestroy(plan->gexec);
+      plan->gexec = nullptr;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->gexec, graph, 0);
-    if (graph) cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    plan->g_f = f_dev;
-    plan->g_q = q_dev;
-    plan->g_ws = workspace;
-  }
-  cudaError_t e = cudaGraphLaunch(plan->gexec, (cudaStream_t)stream);
-  if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
-  return WEF_OK;
+    if (!plan->gexec) {
+      // first call (or new buffers): capture the two launches on the plan's own stream
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      wef_status ls = plan_launch(plan, f_dev, q_dev, workspace, plan->cap_stream);
+      e = cudaStreamEndCapture(plan->cap_stream, &graph);
+      if (ls != WEF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return ls;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->gexec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      plan->g_f = f_dev;
+      plan->g_q = q_dev;
+      plan->g_ws = workspace;
+    }
+    cudaError_t e = cudaGraphLaunch(plan->gexec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    return WEF_OK;
+  });
 }
 
 wef_status wef_plan_autotune(wef_plan plan, const double* f_dev, double* q_dev, void* workspace, int64_t ws_bytes,
                              void* stream, int* chosen) {
-  if (!plan) return set_error(WEF_EINVAL, "wef_plan_autotune: plan is NULL");
-  wef_status st = check_buffers(plan, f_dev, q_dev, workspace, ws_bytes);
-  if (st != WEF_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t ce = cudaEventCreate(&e0);
-  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
-  if (ce != cudaSuccess) {
-    if (e0) cudaEventDestroy(e0);
-    return set_error(WEF_ECUDA, std::string("wef_plan_autotune: ") + cudaGetErrorString(ce));
-  }
-  const bool rf = plan->prec == WEF_RADIAL_FP32;
-  int best_g = plan->granularity;
-  float best = 1e30f;
-  int max_tasks = 1;
-  for (wef_op op : plan->ops) max_tasks = std::max(max_tasks, op->T.prog4.ntasks());
-  if (rf) max_tasks = wef_plan_s::kMaxFork;  // candidates: 1, 2, 4, 8 concurrent shape streams
-  for (int g = 1; g <= 64 && g <= max_tasks; g *= 2) {
+  return wef::guarded("wef_plan_autotune", [&]() -> wef_status {
+    if (!plan) return set_error(WEF_EINVAL, "wef_plan_autotune: plan is NULL");
+    wef_status st = check_buffers(plan, f_dev, q_dev, workspace, ws_bytes);
+    if (st != WEF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+      if (e0) cudaEventDestroy(e0);
+      return set_error(WEF_ECUDA, std::string("wef_plan_autotune: ") + cudaGetErrorString(ce));
+    }
+    const bool rf = plan->prec == WEF_RADIAL_FP32;
+    int best_g = plan->granularity;
+    float best = 1e30f;
+    int max_tasks = 1;
+    for (wef_op op : plan->ops) max_tasks = std::max(max_tasks, op->T.prog4.ntasks());
+    if (rf) max_tasks = wef_plan_s::kMaxFork;  // candidates: 1, 2, 4, 8 concurrent shape streams
+    for (int g = 1; g <= 64 && g <= max_tasks; g *= 2) {
+      if (rf) {
+        plan->nfork = g;
+        plan->granularity = g;
+        if (plan->gexec) {
+          cudaGraphExecDestroy(plan->gexec);
+          plan->gexec = nullptr;
+        }
+      } else {
+        st = set_items(plan, g);
+      }
+      if (st != WEF_OK) break;
+      st = plan_launch(plan, f_dev, q_dev, workspace, s);  // warm-up
+      if (st == WEF_OK) cudaEventRecord(e0, s);
+      for (int r = 0; r < 2 && st == WEF_OK; ++r) st = plan_launch(plan, f_dev, q_dev, workspace, s);
+      if (st != WEF_OK) break;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        st = set_error(WEF_ECUDA, "wef_plan_autotune: timing failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_g = g;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != WEF_OK) return st;
     if (rf) {
-      plan->nfork = g;
-      plan->granularity = g;
+      plan->nfork = plan->granularity = best_g;
       if (plan->gexec) {
         cudaGraphExecDestroy(plan->gexec);
         plan->gexec = nullptr;
       }
     } else {
-      st = set_items(plan, g);
+      st = set_items(plan, best_g);
+      if (st != WEF_OK) return st;
     }
-    if (st != WEF_OK) break;
-    st = plan_launch(plan, f_dev, q_dev, workspace, s);  // warm-up
-    if (st == WEF_OK) cudaEventRecord(e0, s);
-    for (int r = 0; r < 2 && st == WEF_OK; ++r) st = plan_launch(plan, f_dev, q_dev, workspace, s);
-    if (st != WEF_OK) break;
-    cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      st = set_error(WEF_ECUDA, "wef_plan_autotune: timing failed");
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) {
-      best = ms;
-      best_g = g;
-    }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (st != WEF_OK) return st;
-  if (rf) {
-    plan->nfork = plan->granularity = best_g;
-    if (plan->gexec) {
-      cudaGraphExecDestroy(plan->gexec);
-      plan->gexec = nullptr;
-    }
-  } else {
-    st = set_items(plan, best_g);
-    if (st != WEF_OK) return st;
-  }
-  cache_store(plan->key, best_g);
-  if (chosen) *chosen = best_g;
-  return WEF_OK;
+    cache_store(plan->key, best_g);
+    if (chosen) *chosen = best_g;
+    return WEF_OK;
+  });
 }
 
 wef_status wef_plan_status(wef_plan plan, int reset) {

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -90,21 +91,20 @@ extern "C" {
 const char* wef_last_error(void) { return g_err.c_str(); }
 
 wef_status wef_create(int kmax, int lmax, double gamma, wef_op* out) {
-  if (!out) return fail(WEF_EINVAL, "wef_create: out is NULL");
-  *out = nullptr;
-  if (kmax < 0 || kmax > WEF_MAX_KMAX || lmax < 0 || lmax > WEF_MAX_LMAX)
-    return fail(WEF_ESHAPE, "wef_create: Kmax must be in [0,16] and Lmax in [0,20]");
-  if (!(gamma >= 0.0 && gamma <= 2.0)) return fail(WEF_EINVAL, "wef_create: gamma must be in [0, 2]");
-  wef_operator* op = new (std::nothrow) wef_operator();
-  if (!op) return fail(WEF_ENOMEM, "wef_create: host allocation failed");
-  op->gamma = gamma;
-  std::string err = build_tables(kmax, lmax, op->T);
-  if (!err.empty()) {
-    delete op;
-    return fail(WEF_ESHAPE, "wef_create: " + err);
-  }
-  *out = op;
-  return WEF_OK;
+  return wef::guarded("wef_create", [&]() -> wef_status {
+    if (!out) return fail(WEF_EINVAL, "wef_create: out is NULL");
+    *out = nullptr;
+    if (kmax < 0 || kmax > WEF_MAX_KMAX || lmax < 0 || lmax > WEF_MAX_LMAX)
+      return fail(WEF_ESHAPE, "wef_create: Kmax must be in [0,16] and Lmax in [0,20]");
+    if (!(gamma >= 0.0 && gamma <= 2.0)) return fail(WEF_EINVAL, "wef_create: gamma must be in [0, 2]");
+    std::unique_ptr<wef_operator> op(new (std::nothrow) wef_operator());
+    if (!op) return fail(WEF_ENOMEM, "wef_create: host allocation failed");
+    op->gamma = gamma;
+    std::string err = build_tables(kmax, lmax, op->T);
+    if (!err.empty()) return fail(WEF_ESHAPE, "wef_create: " + err);
+    *out = op.release();
+    return WEF_OK;
+  });
 }
 
 wef_status wef_sizes(wef_op op, int64_t* n_per_cell, int64_t* n_channels, int64_t* n_gaunt, int64_t* core_len) {
@@ -129,82 +129,84 @@ wef_status wef_gaunt_coo(wef_op op, int32_t* q1, int32_t* q2, int32_t* q3, int32
 }
 
 wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigned flags) {
-  if (!op || !R_host) return fail(WEF_EINVAL, "wef_upload_core: NULL argument");
-  const Tables& T = op->T;
-  const int K = T.K;
-  const int64_t K3 = (int64_t)K * K * K;
-  const int64_t NT = (int64_t)T.chans.size();
-  if (len != NT * K3) return fail(WEF_ESHAPE, "wef_upload_core: len must be N_T*K^3");
-  if (op->d_status) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev != op->device)
-      return fail(WEF_EINVAL, "wef_upload_core: the current device is not the one the operator was set up on");
-  }
-  cudaError_t de = ensure_device(op);
-  if (de != cudaSuccess) return cuda_fail(de, "wef_upload_core: device set-up");
-  std::vector<double> R(R_host, R_host + len);
-  if (flags & WEF_CORE_APPLY_NULLSPACE) {
-    for (int64_t c = 0; c < NT; ++c) {
-      const Channel& h = T.chans[c];
-      double* Rc = &R[c * K3];
-      if (h.l1 == 0) {
-        std::fill(Rc, Rc + K * K, 0.0);                              // mass, k1 = 0
-        if (K > 1) std::fill(Rc + K * K, Rc + 2 * K * K, 0.0);       // energy, k1 = 1
-      }
-      if (h.l1 == 1) std::fill(Rc, Rc + K * K, 0.0);                 // momentum, k1 = 0
-      if (h.l1 == 0 && h.l2 == 0 && h.l3 == 0)
-        for (int k1 = 0; k1 < K; ++k1) Rc[(int64_t)k1 * K * K] = 0.0;  // detailed balance
+  return wef::guarded("wef_upload_core", [&]() -> wef_status {
+    if (!op || !R_host) return fail(WEF_EINVAL, "wef_upload_core: NULL argument");
+    const Tables& T = op->T;
+    const int K = T.K;
+    const int64_t K3 = (int64_t)K * K * K;
+    const int64_t NT = (int64_t)T.chans.size();
+    if (len != NT * K3) return fail(WEF_ESHAPE, "wef_upload_core: len must be N_T*K^3");
+    if (op->d_status) {
+      int dev = -1;
+      if (cudaGetDevice(&dev) != cudaSuccess || dev != op->device)
+        return fail(WEF_EINVAL, "wef_upload_core: the current device is not the one the operator was set up on");
     }
-  }
-  // symmetrised core Rt[sc] = R[c] + R[c']^{T23}, FP64 layout [sc][k3][k1][k2]
-  const int NS = (int)T.sym_chan.size();
-  std::vector<double> R64((size_t)NS * K3);
-  for (int s = 0; s < NS; ++s) {
-    const double* A = &R[(int64_t)T.sym_chan[s] * K3];
-    const double* B = &R[(int64_t)T.sym_partner[s] * K3];
-    for (int k1 = 0; k1 < K; ++k1)
-      for (int k2 = 0; k2 < K; ++k2)
-        for (int k3 = 0; k3 < K; ++k3) {
-          const double v = A[(k1 * K + k2) * K + k3] + B[(k1 * K + k3) * K + k2];
-          R64[(((size_t)s * K + k3) * K + k1) * K + k2] = v;
+    cudaError_t de = ensure_device(op);
+    if (de != cudaSuccess) return cuda_fail(de, "wef_upload_core: device set-up");
+    std::vector<double> R(R_host, R_host + len);
+    if (flags & WEF_CORE_APPLY_NULLSPACE) {
+      for (int64_t c = 0; c < NT; ++c) {
+        const Channel& h = T.chans[c];
+        double* Rc = &R[c * K3];
+        if (h.l1 == 0) {
+          std::fill(Rc, Rc + K * K, 0.0);                              // mass, k1 = 0
+          if (K > 1) std::fill(Rc + K * K, Rc + 2 * K * K, 0.0);       // energy, k1 = 1
         }
-  }
-  // packed tensor-core B tiles of Rt[sc][k1][k2][k3] (from the FP64 layout [sc][k3][k1][k2])
-  std::vector<uint8_t> Bb, Bt;
-  if (K <= 17) {
-    const int nb = tc_b_tile_bytes(K, false), nt = tc_b_tile_bytes(K, true);
-    Bb.resize((size_t)NS * nb);
-    Bt.resize((size_t)NS * nt);
-    std::vector<double> Rt((size_t)K3);
+        if (h.l1 == 1) std::fill(Rc, Rc + K * K, 0.0);                 // momentum, k1 = 0
+        if (h.l1 == 0 && h.l2 == 0 && h.l3 == 0)
+          for (int k1 = 0; k1 < K; ++k1) Rc[(int64_t)k1 * K * K] = 0.0;  // detailed balance
+      }
+    }
+    // symmetrised core Rt[sc] = R[c] + R[c']^{T23}, FP64 layout [sc][k3][k1][k2]
+    const int NS = (int)T.sym_chan.size();
+    std::vector<double> R64((size_t)NS * K3);
     for (int s = 0; s < NS; ++s) {
+      const double* A = &R[(int64_t)T.sym_chan[s] * K3];
+      const double* B = &R[(int64_t)T.sym_partner[s] * K3];
+      for (int k1 = 0; k1 < K; ++k1)
+        for (int k2 = 0; k2 < K; ++k2)
+          for (int k3 = 0; k3 < K; ++k3) {
+            const double v = A[(k1 * K + k2) * K + k3] + B[(k1 * K + k3) * K + k2];
+            R64[(((size_t)s * K + k3) * K + k1) * K + k2] = v;
+          }
+    }
+    // packed tensor-core B tiles of Rt[sc][k1][k2][k3] (from the FP64 layout [sc][k3][k1][k2])
+    std::vector<uint8_t> Bb, Bt;
+    if (K <= 17) {
+      const int nb = tc_b_tile_bytes(K, false), nt = tc_b_tile_bytes(K, true);
+      Bb.resize((size_t)NS * nb);
+      Bt.resize((size_t)NS * nt);
+      std::vector<double> Rt((size_t)K3);
+      for (int s = 0; s < NS; ++s) {
+        for (int k1 = 0; k1 < K; ++k1)
+          for (int k2 = 0; k2 < K; ++k2)
+            for (int k3 = 0; k3 < K; ++k3)
+              Rt[((size_t)k1 * K + k2) * K + k3] = R64[(((size_t)s * K + k3) * K + k1) * K + k2];
+        tc_pack_b_tile(K, false, Rt.data(), &Bb[(size_t)s * nb]);
+        tc_pack_b_tile(K, true, Rt.data(), &Bt[(size_t)s * nt]);
+      }
+    }
+    // FP32 copy for the radial-first path, layout [sc][k1][k3][k2 -> KP4]: k2, the index the
+    // first radial stage contracts, fastest and padded with zeros to whole float4s.
+    const int KP4 = rf_k2_padded(K);
+    std::vector<float> R32((size_t)NS * K * K * KP4, 0.0f);
+    for (int s = 0; s < NS; ++s)
       for (int k1 = 0; k1 < K; ++k1)
         for (int k2 = 0; k2 < K; ++k2)
           for (int k3 = 0; k3 < K; ++k3)
-            Rt[((size_t)k1 * K + k2) * K + k3] = R64[(((size_t)s * K + k3) * K + k1) * K + k2];
-      tc_pack_b_tile(K, false, Rt.data(), &Bb[(size_t)s * nb]);
-      tc_pack_b_tile(K, true, Rt.data(), &Bt[(size_t)s * nt]);
-    }
-  }
-  // FP32 copy for the radial-first path, layout [sc][k1][k3][k2 -> KP4]: k2, the index the
-  // first radial stage contracts, fastest and padded with zeros to whole float4s.
-  const int KP4 = rf_k2_padded(K);
-  std::vector<float> R32((size_t)NS * K * K * KP4, 0.0f);
-  for (int s = 0; s < NS; ++s)
-    for (int k1 = 0; k1 < K; ++k1)
-      for (int k2 = 0; k2 < K; ++k2)
-        for (int k3 = 0; k3 < K; ++k3)
-          R32[(((size_t)s * K + k1) * K + k3) * KP4 + k2] = (float)R64[(((size_t)s * K + k3) * K + k1) * K + k2];
-  op->release_core();
-  cudaError_t e = upload(&op->d_R64, R64);
-  if (e == cudaSuccess) e = upload(&op->d_R32, R32);
-  if (e == cudaSuccess) e = upload(&op->d_Bbf16, Bb);
-  if (e == cudaSuccess) e = upload(&op->d_Btf32, Bt);
-  if (e != cudaSuccess) {
+            R32[(((size_t)s * K + k1) * K + k3) * KP4 + k2] = (float)R64[(((size_t)s * K + k3) * K + k1) * K + k2];
     op->release_core();
-    return cuda_fail(e, "wef_upload_core");
-  }
-  op->has_core = true;
-  return WEF_OK;
+    cudaError_t e = upload(&op->d_R64, R64);
+    if (e == cudaSuccess) e = upload(&op->d_R32, R32);
+    if (e == cudaSuccess) e = upload(&op->d_Bbf16, Bb);
+    if (e == cudaSuccess) e = upload(&op->d_Btf32, Bt);
+    if (e != cudaSuccess) {
+      op->release_core();
+      return cuda_fail(e, "wef_upload_core");
+    }
+    op->has_core = true;
+    return WEF_OK;
+  });
 }
 
 wef_status wef_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int64_t* bytes) {
@@ -223,65 +225,69 @@ wef_status wef_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int
 
 wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t ncells, wef_precision prec,
                         void* workspace, int64_t workspace_bytes, void* stream) {
-  if (!op) return fail(WEF_EINVAL, "wef_evaluate: op is NULL");
-  if (!valid_precision(prec)) return fail(WEF_EINVAL, "wef_evaluate: unknown precision");
-  if (ncells < 0) return fail(WEF_EINVAL, "wef_evaluate: ncells < 0");
-  if (ncells == 0) return WEF_OK;
-  if (!f_dev || !q_dev || !workspace) return fail(WEF_EINVAL, "wef_evaluate: NULL buffer");
-  if (!op->has_core) return fail(WEF_ENOCORE, "wef_evaluate: no core uploaded");
-  if (((uintptr_t)workspace & 255) != 0) return fail(WEF_EINVAL, "wef_evaluate: workspace not 256-byte aligned");
-  int64_t need = 0;
-  if (wef_workspace_size(op, ncells, prec, &need) != WEF_OK) return WEF_EINVAL;
-  if (workspace_bytes < need) return fail(WEF_EINVAL, "wef_evaluate: workspace too small");
-  if (ncells > (int64_t)65535 * 32 * 1024) return fail(WEF_EINVAL, "wef_evaluate: ncells too large");
-  {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev != op->device)
-      return fail(WEF_EINVAL, "wef_evaluate: the current device is not the one the core was uploaded on");
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  const int K = op->T.K, NQ = op->T.NQ;
-  if (prec == WEF_RADIAL_FP32) {
-    const RadialProgram& RP = op->T.rprog;
-    DevRadial r{(const int4*)op->r_tasks, (const int4*)op->r_chans, (const int4*)op->r_blocks,
-                (const int4*)op->r_uents, (const double2*)op->r_pw, op->r_order,
-                (int)RP.task_cost.size(), RP.n1max};
-    cudaError_t er = launch_rf(K, f_dev, (float*)((char*)workspace + 256), (int*)workspace, q_dev, ncells, NQ, r,
-                               op->d_R32, op->sms, s, op->trace_start, op->trace_stop);
-    if (er != cudaSuccess) return cuda_fail(er, "wef_evaluate: radial-first kernels");
+  return wef::guarded("wef_evaluate", [&]() -> wef_status {
+    if (!op) return fail(WEF_EINVAL, "wef_evaluate: op is NULL");
+    if (!valid_precision(prec)) return fail(WEF_EINVAL, "wef_evaluate: unknown precision");
+    if (ncells < 0) return fail(WEF_EINVAL, "wef_evaluate: ncells < 0");
+    if (ncells == 0) return WEF_OK;
+    if (!f_dev || !q_dev || !workspace) return fail(WEF_EINVAL, "wef_evaluate: NULL buffer");
+    if (!op->has_core) return fail(WEF_ENOCORE, "wef_evaluate: no core uploaded");
+    if (((uintptr_t)workspace & 255) != 0) return fail(WEF_EINVAL, "wef_evaluate: workspace not 256-byte aligned");
+    int64_t need = 0;
+    if (wef_workspace_size(op, ncells, prec, &need) != WEF_OK) return WEF_EINVAL;
+    if (workspace_bytes < need) return fail(WEF_EINVAL, "wef_evaluate: workspace too small");
+    if (ncells > (int64_t)65535 * 32 * 1024) return fail(WEF_EINVAL, "wef_evaluate: ncells too large");
+    {
+      int dev = -1;
+      if (cudaGetDevice(&dev) != cudaSuccess || dev != op->device)
+        return fail(WEF_EINVAL, "wef_evaluate: the current device is not the one the core was uploaded on");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = op->T.K, NQ = op->T.NQ;
+    if (prec == WEF_RADIAL_FP32) {
+      const RadialProgram& RP = op->T.rprog;
+      DevRadial r{(const int4*)op->r_tasks, (const int4*)op->r_chans, (const int4*)op->r_blocks,
+                  (const int4*)op->r_uents, (const double2*)op->r_pw, op->r_order,
+                  (int)RP.task_cost.size(), RP.n1max};
+      cudaError_t er = launch_rf(K, f_dev, (float*)((char*)workspace + 256), (int*)workspace, q_dev, ncells, NQ, r,
+                                 op->d_R32, op->sms, s, op->trace_start, op->trace_stop);
+      if (er != cudaSuccess) return cuda_fail(er, "wef_evaluate: radial-first kernels");
+      return WEF_OK;
+    }
+    double* ftile = (double*)workspace;
+    cudaError_t e = launch_tile_f(f_dev, ftile, ncells, K, NQ, s);
+    if (e != cudaSuccess) return cuda_fail(e, "wef_evaluate: tile kernel");
+    // chunk count: enough CTAs for several waves of the GPU
+    const int v = prec == WEF_FP64 ? 0 : 1;
+    const wef_operator::DevProg& D = op->dp[v];
+    const int64_t ntiles = (ncells + 31) / 32;
+    const int64_t want = 4LL * op->sms;
+    int idx = 0;
+    while (idx + 1 < (int)D.chunk_n.size() && ntiles * D.chunk_n[idx] < want) ++idx;
+    const Program& P = v == 0 ? op->T.prog1 : op->T.prog4;
+    DevProgram p{D.prog, (const int4*)D.groups, (const double2*)D.gw, D.off, P.ntasks()};
+    if (op->trace_start) cudaEventRecord(op->trace_start, s);
+    if (prec == WEF_FP64)
+      e = launch_fp64(K, ftile, q_dev, ncells, NQ, p, D.chunks + D.chunk_pos[idx], D.chunk_n[idx], op->d_R64, s);
+    else
+      e = launch_tc(K, prec == WEF_MIXED_TF32, ftile, q_dev, ncells, NQ, p, D.chunks + D.chunk_pos[idx], D.chunk_n[idx],
+                    prec == WEF_MIXED_TF32 ? op->d_Btf32 : op->d_Bbf16, op->d_status, s);
+    if (op->trace_stop) cudaEventRecord(op->trace_stop, s);
+    if (e != cudaSuccess) return cuda_fail(e, "wef_evaluate: contraction kernel");
     return WEF_OK;
-  }
-  double* ftile = (double*)workspace;
-  cudaError_t e = launch_tile_f(f_dev, ftile, ncells, K, NQ, s);
-  if (e != cudaSuccess) return cuda_fail(e, "wef_evaluate: tile kernel");
-  // chunk count: enough CTAs for several waves of the GPU
-  const int v = prec == WEF_FP64 ? 0 : 1;
-  const wef_operator::DevProg& D = op->dp[v];
-  const int64_t ntiles = (ncells + 31) / 32;
-  const int64_t want = 4LL * op->sms;
-  int idx = 0;
-  while (idx + 1 < (int)D.chunk_n.size() && ntiles * D.chunk_n[idx] < want) ++idx;
-  const Program& P = v == 0 ? op->T.prog1 : op->T.prog4;
-  DevProgram p{D.prog, (const int4*)D.groups, (const double2*)D.gw, D.off, P.ntasks()};
-  if (op->trace_start) cudaEventRecord(op->trace_start, s);
-  if (prec == WEF_FP64)
-    e = launch_fp64(K, ftile, q_dev, ncells, NQ, p, D.chunks + D.chunk_pos[idx], D.chunk_n[idx], op->d_R64, s);
-  else
-    e = launch_tc(K, prec == WEF_MIXED_TF32, ftile, q_dev, ncells, NQ, p, D.chunks + D.chunk_pos[idx], D.chunk_n[idx],
-                  prec == WEF_MIXED_TF32 ? op->d_Btf32 : op->d_Bbf16, op->d_status, s);
-  if (op->trace_stop) cudaEventRecord(op->trace_stop, s);
-  if (e != cudaSuccess) return cuda_fail(e, "wef_evaluate: contraction kernel");
-  return WEF_OK;
+  });
 }
 
 wef_status wef_core_build(wef_op op, int pad_rad, int pad_ang, double* R_out, int64_t len) {
-  if (!op || !R_out) return fail(WEF_EINVAL, "wef_core_build: NULL argument");
-  const int64_t K = op->T.K;
-  if (len != (int64_t)op->T.chans.size() * K * K * K) return fail(WEF_ESHAPE, "wef_core_build: len must be N_T*K^3");
-  if (pad_rad < 0 || pad_ang < 0 || pad_rad > 200 || pad_ang > 200) return fail(WEF_EINVAL, "wef_core_build: bad padding");
-  std::string err = core_build(op->T, op->gamma, pad_rad, pad_ang, R_out);
-  if (!err.empty()) return fail(WEF_EINVAL, "wef_core_build: " + err);
-  return WEF_OK;
+  return wef::guarded("wef_core_build", [&]() -> wef_status {
+    if (!op || !R_out) return fail(WEF_EINVAL, "wef_core_build: NULL argument");
+    const int64_t K = op->T.K;
+    if (len != (int64_t)op->T.chans.size() * K * K * K) return fail(WEF_ESHAPE, "wef_core_build: len must be N_T*K^3");
+    if (pad_rad < 0 || pad_ang < 0 || pad_rad > 200 || pad_ang > 200) return fail(WEF_EINVAL, "wef_core_build: bad padding");
+    std::string err = core_build(op->T, op->gamma, pad_rad, pad_ang, R_out);
+    if (!err.empty()) return fail(WEF_EINVAL, "wef_core_build: " + err);
+    return WEF_OK;
+  });
 }
 
 wef_status wef_flops(wef_op op, wef_precision prec, double* fp64_flops_per_cell, double* tc_flops_per_cell) {

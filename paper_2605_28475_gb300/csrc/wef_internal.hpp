@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 
 #include "tables.hpp"
@@ -130,6 +132,30 @@ cudaError_t launch_ragged_tc(bool tf32, int max_k, int nsm, const RaggedShape* s
 
 // Record `msg` as this thread's last error (returned by wef_last_error) and return `s`.
 wef_status set_error(wef_status s, const std::string& msg);
+
+// Runs the body of a C entry point so that no C++ exception crosses the ABI: a failed
+// host allocation becomes WEF_ENOMEM, any other exception WEF_EINVAL, with the message
+// recorded when recording it is still possible.
+template <class F>
+wef_status guarded(const char* name, F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    try {
+      return set_error(WEF_ENOMEM, std::string(name) + ": host allocation failed");
+    } catch (...) {
+      return WEF_ENOMEM;
+    }
+  } catch (const std::exception& e) {
+    try {
+      return set_error(WEF_EINVAL, std::string(name) + ": " + e.what());
+    } catch (...) {
+      return WEF_EINVAL;
+    }
+  } catch (...) {
+    return WEF_EINVAL;
+  }
+}
 
 std::string core_build(const Tables& T, double gamma, int pad_rad, int pad_ang, double* R);
 
