@@ -1,4 +1,5 @@
-"""Host-side logic of the request loop: the arena allocator and the Poisson generator."""
+"""Host-side logic of the request loop: the arena allocator, the Poisson generator, batch
+packing and the scheduling loop (driven with a fake server whose batches finish at once)."""
 import numpy as np
 import pytest
 
@@ -48,3 +49,57 @@ def test_pack_batch_caps():
     # the oldest request goes alone even if it exceeds both caps
     assert [r.f.shape[0] for r in serve.pack_batch([mk(5000)] + w, 450, cost, 0.35)] == [5000]
     assert serve.pack_batch([], 450) == []
+
+
+class _FakeServer:
+    """The interface run() drives, with batches that finish at the next poll: it packs the
+    same batches as the real server (pack_batch), refuses requests above a cell limit, and
+    has `slots` batches in flight at most."""
+
+    def __init__(self, max_cells_ever, slots=2, max_batch_cells=64):
+        self.max_cells_ever, self.slots, self.max_batch_cells = max_cells_ever, slots, max_batch_cells
+        self.in_flight, self.completed, self.rejected, self.batches = [], [], [], 0
+
+    def fits_ever(self, r):
+        return r.f.shape[0] <= self.max_cells_ever
+
+    def try_launch(self, waiting, now):
+        if len(self.in_flight) >= self.slots or not waiting:
+            return False
+        chosen = serve.pack_batch(waiting, self.max_batch_cells)
+        ids = {id(r) for r in chosen}
+        waiting[:] = [r for r in waiting if id(r) not in ids]
+        for r in chosen:
+            r.admitted = now
+        self.in_flight.append(chosen)
+        self.batches += 1
+        return True
+
+    def poll(self, now_fn):
+        t, n = now_fn(), 0
+        for batch in self.in_flight:
+            for r in batch:
+                r.done = t
+                self.completed.append(r)
+                n += 1
+        self.in_flight = []
+        return n
+
+    def idle(self):
+        return not self.in_flight
+
+
+def test_run_loop_accounts_for_every_request():
+    """Every request is completed or rejected exactly once, in its shape's batches, never
+    before it arrived; the summary counts agree with the server's records."""
+    mk = lambda sh, n, s: np.zeros((n, 1))  # noqa: E731
+    reqs = serve.poisson_requests(400.0, 0.25, [(8, 8), (12, 12)], 100, seed=4, make_cells=mk)
+    srv = _FakeServer(max_cells_ever=80)
+    out = serve.run(srv, reqs)
+    assert out["requests"] == len(reqs) == out["completed"] + out["rejected"]
+    assert {id(r) for r in srv.completed}.isdisjoint({id(r) for r in srv.rejected})
+    assert all(r.f.shape[0] > 80 for r in srv.rejected) and all(r.f.shape[0] <= 80 for r in srv.completed)
+    assert all(r.arrival <= r.admitted <= r.done for r in srv.completed)
+    assert out["cells"] == sum(r.f.shape[0] for r in srv.completed)
+    assert out["p50_ms"] is not None and out["p50_ms"] <= out["p99_ms"]
+    assert out["batches"] == srv.batches <= out["completed"]
