@@ -29,3 +29,21 @@ def test_angular_first_all_cores_figure():
     assert r.returncode == 0, r.stderr[-2000:]
     d = json.loads(r.stdout.strip().splitlines()[-1])
     assert d["cores"] == 2 and d["value"] > 0 and d["unit"] == "cells/s" and d["cpu_model"]
+
+
+def test_clock_summary_parsing():
+    """The clocks object of the benchmark line from nvidia-smi CSV samples: median SM clock,
+    maximum clock, and every throttle reason seen active in any sample."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    s = bench.ClockSampler(0)
+    s.lines = ["2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "2055, 2070, 1390.2, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+               "[N/A], 2070, 1380.0, 0x0, Not Active, Not Active, Not Active, Not Active",  # unparsable: skipped
+               "2040, 2070, 1395.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active"]
+    d = s.summary()
+    assert d["sm_mhz"] == 2055.0 and d["sm_max_mhz"] == 2070.0 and d["samples"] == 3
+    assert d["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    s.lines = []
+    assert s.summary()["reasons"] == ["unsampled"]
