@@ -1,5 +1,7 @@
-// Radial-first contraction kernel, shared by the two translation units that instantiate
-// it with the FP64 accumulators in shared memory or in tensor memory (see kernels_rf.cu).
+// Radial-first contraction kernel (the paper's Sec. 4.5.3 ordering: both radial stages
+// first, then the Gaunt reduction of Sec. 4.1-4.2 and the Sec. 4.4 projection), shared by
+// the two translation units that instantiate it with the FP64 accumulators in shared
+// memory or in tensor memory (see kernels_rf.cu).
 #pragma once
 #include <cuda_runtime.h>
 
