@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ncells", type=int, default=NCELLS)
     ap.add_argument("--kl", type=int, default=KMAX, help="Kmax = Lmax of the main workload (default 12)")
-    ap.add_argument("--cpu-sample-rows", type=int, default=384)
+    ap.add_argument("--cpu-sample-rows", type=int, default=None,
+                    help="output rows of each sampled cell the CPU oracle evaluates (default: all N)")
     ap.add_argument("--cpu-sample-cells", type=int, default=4)
     ap.add_argument("--workload", default="kl12",
                     choices=["kl12", "maxwell4", "hs8", "ragged", "serve", "baselines", "rk4", "core"],
@@ -122,16 +123,26 @@ def cpu_model():
     return platform.machine()
 
 
-def cpu_baseline(sample_cells, sample_rows, seed=3, with_angular_first=False):
+REFERENCE_STEP_ROWS = 384  # output rows per reference-arm step: a few seconds of CPU work
+
+
+def sample_rows_of(rows):
+    """Output rows per sampled cell for the CPU oracle: all N by default, at most N."""
+    N = (KMAX + 1) * (LMAX + 1) ** 2
+    return N if rows is None or rows <= 0 else min(int(rows), N)
+
+
+def cpu_baseline(sample_cells, sample_rows=None, seed=3, with_angular_first=False):
     """The oracle (dense FP64 CPU contraction) timed on a bounded sample of the workload:
-    `sample_cells` cells and `sample_rows` of the N output rows, scaled to cells/s.  With
-    `with_angular_first`, also the paper's factorised contraction in numpy (a CPU
-    comparison point, reported inside this object)."""
+    `sample_cells` cells and `sample_rows` of the N output rows (default all), scaled to
+    cells/s.  With `with_angular_first`, also the paper's factorised contraction in numpy
+    (a CPU comparison point, reported inside this object)."""
     import wef_inputs as wi
     from oracle import dense, gaunt
 
     K, NQ = KMAX + 1, (LMAX + 1) ** 2
     N = K * NQ
+    sample_rows = sample_rows_of(sample_rows)
     R = wi.random_core(len(gaunt.channels(LMAX)), KMAX, seed=11)  # timing does not depend on the values
     f = wi.two_maxwellians(KMAX, LMAX, sample_cells, seed=seed).reshape(sample_cells, -1)
     op = dense.DenseOperator(KMAX, LMAX, dense.conservation_zeroing(R, LMAX))
@@ -290,12 +301,13 @@ def run_reference(args, rank, world):
     cells x `--cpu-sample-rows` output rows); rank 0 only (no GPU work)."""
     if rank != 0:
         return
+    rows = args.cpu_sample_rows or REFERENCE_STEP_ROWS  # per step; the headline's sample takes all rows
     for _ in range(args.warmup):
-        cpu_baseline(args.cpu_sample_cells, args.cpu_sample_rows)
+        cpu_baseline(args.cpu_sample_cells, rows)
     t0 = time.perf_counter()
-    samples = [cpu_baseline(args.cpu_sample_cells, args.cpu_sample_rows) for _ in range(max(args.steps, 1))]
+    samples = [cpu_baseline(args.cpu_sample_cells, rows) for _ in range(max(args.steps, 1))]
     dt = time.perf_counter() - t0
-    cells_per_step = args.cpu_sample_cells * args.cpu_sample_rows / ((KMAX + 1) * (LMAX + 1) ** 2)
+    cells_per_step = args.cpu_sample_cells * sample_rows_of(rows) / ((KMAX + 1) * (LMAX + 1) ** 2)
     value = cells_per_step * len(samples) / dt
     cb = dict(samples[-1])
     cb["value"] = value
