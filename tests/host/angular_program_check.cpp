@@ -2,12 +2,18 @@
 #include <cstdio>
 #include <cmath>
 #include <random>
+#include <utility>
 #include <vector>
 #include "../../paper_2605_28475_gb300/csrc/tables.hpp"
 using namespace wef;
 int main() {
   int bad = 0;
-  for (int L : {0, 1, 2, 3, 4, 6, 8, 12, 16}) for (int km : {0, 1, 4, 12}) {
+  // the grid, then the largest operator the library accepts (Kmax = 16, Lmax = 20)
+  std::vector<std::pair<int, int>> shapes;
+  for (int L : {0, 1, 2, 3, 4, 6, 8, 12, 16}) for (int km : {0, 1, 4, 12}) shapes.push_back({L, km});
+  shapes.push_back({20, 16});
+  for (const auto& sh : shapes) {
+    const int L = sh.first, km = sh.second;
     Tables T; std::string e = build_tables(km, L, T); if (!e.empty()) { printf("err %s\n", e.c_str()); return 1; }
     const int K = T.K, NQ = T.NQ, NS = (int)T.sym_chan.size(), NT = (int)T.chans.size();
     std::mt19937_64 rng(km * 100 + L); std::normal_distribution<double> nd;
