@@ -153,3 +153,21 @@ def test_flop_counts_match_the_coo_table(km, lm):
     assert fp64 == 2 * K * E
     assert fp32 == 2 * K**3 * len(groups) + 2 * K**2 * len(pairs)
     assert plain == 2 * K**2 * len(rank1) + 2 * K * E + 2 * K**3 * len(slices)
+
+
+def test_plain_c_client(tmp_path):
+    """include/wef.h is a C header: a C99 program (-pedantic -Werror) that includes it, links
+    libwef.so and calls the host-only entry points runs and checks its results."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(W.LIB_PATH)
+    exe = str(tmp_path / "c_abi_client")
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-o", exe,
+                    os.path.join(ROOT, "tests", "host", "c_abi_client.c"), f"-L{libdir}", "-lwef",
+                    f"-Wl,-rpath,{libdir}", "-Wl,--allow-shlib-undefined"], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
