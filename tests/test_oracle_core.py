@@ -36,6 +36,30 @@ def test_krook_wu_isotropic_maxwell():
         assert np.allclose(Q, Qex, rtol=0, atol=1e-14)
 
 
+def test_maxwell_stress_relaxation_nonlinear():
+    """Maxwell molecules (§5.2): the traceless pressure tensor relaxes exactly at the first
+    l = 2 rate, whatever else f contains.  In the basis, phi_000 = 1 and phi_{0,(1,m)} =
+    v_(y,z,x), so c_000 is the density and c_{0,(1,.)} the momentum density p, and the
+    k = 0, l = 2 rows of the full nonlinear operator are
+        Q_{0,(2,m)} = lambda_{0,2} (c_000 c_{0,(2,m)} - N_02 |p|^2 Y_2m(p / |p|)),
+    the Galerkin form of d(rho P_ij)/dt = -nu rho (P_ij - p delta_ij) with P the central
+    second moment.  Checked on random f with every mode (Kmax = Lmax = 3) against the
+    closed-form lambda_{0,2}: all other products of modes must cancel in these rows."""
+    km, lm = 3, 3
+    K, NQ = km + 1, (lm + 1) ** 2
+    op = dense.DenseOperator(km, lm, dense.conservation_zeroing(core.core(km, lm, 0.0), lm))
+    lam = _wcu_closed_form(0, 2)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        c = 0.3 * rng.standard_normal((K, NQ))
+        c[0, 0] = 1.3
+        Q = op.evaluate(c.reshape(1, -1)).reshape(K, NQ)
+        p = np.array([c[0, 3], c[0, 1], c[0, 2]])  # (x, y, z) from m = 1, -1, 0
+        Y2 = basis.real_sh_all(2, (p / np.linalg.norm(p))[None, :])[0, 4:9]
+        expect = lam * (c[0, 0] * c[0, 4:9] - basis.radial_norm(0, 2) * (p @ p) * Y2)
+        assert np.max(np.abs(Q[0, 4:9] - expect)) < 1e-13 * np.max(np.abs(expect))
+
+
 def _wcu_closed_form(k, l):
     """lambda_kl = 1/2 int_{-1}^{1} [c^{2k+l} P_l(c) + s^{2k+l} P_l(s) - 1 - delta_k0 delta_l0] dx,
     c = sqrt((1+x)/2), s = sqrt((1-x)/2): Maxwell molecules, B = 1/(4 pi), unit density."""
