@@ -1,16 +1,19 @@
-"""Pins of the oracle's kinematic core quadrature (§3, §4.3, §4.4, §5.2, §5.3).
+"""Pins of the oracle's kinematic core quadrature (§3, §4.3, §4.4, §5.1, §5.2, §5.3).
 
 Each pin is fixed by something other than the oracle: closed forms (Krook-Wu
-moment system, Wang Chang-Uhlenbeck eigenvalues), values the paper prints
-(Table 3, Table 5), an exact brute-force 8D evaluation of the weak form, and
-the analytic conservation laws that the raw quadrature must already satisfy
-to rounding before the §4.4 zeroing."""
+moment system, exact stress relaxation and moment closure of Maxwell molecules,
+Wang Chang-Uhlenbeck eigenvalues), values the paper prints (Table 3, Table 5),
+exact brute-force 8D evaluations of the weak form (Maxwell molecules in (v, w);
+any power law in centre-of-mass and relative velocity), the padding convergence
+of §5.1, and the analytic conservation laws that the raw quadrature must already
+satisfy to rounding before the §4.4 zeroing."""
 import math
 
 import numpy as np
 import pytest
 from scipy import special
 
+import wef_inputs as wi
 from conftest import golden
 from oracle import basis, core, dense, gaunt
 
@@ -36,7 +39,13 @@ def test_krook_wu_isotropic_maxwell():
         assert np.allclose(Q, Qex, rtol=0, atol=1e-14)
 
 
-def test_maxwell_stress_relaxation_nonlinear():
+@pytest.fixture(scope="module")
+def maxwell_33():
+    """The dense Maxwell-molecule operator at Kmax = Lmax = 3 (oracle core, zeroed)."""
+    return dense.DenseOperator(3, 3, dense.conservation_zeroing(core.core(3, 3, 0.0), 3))
+
+
+def test_maxwell_stress_relaxation_nonlinear(maxwell_33):
     """Maxwell molecules (§5.2): the traceless pressure tensor relaxes exactly at the first
     l = 2 rate, whatever else f contains.  In the basis, phi_000 = 1 and phi_{0,(1,m)} =
     v_(y,z,x), so c_000 is the density and c_{0,(1,.)} the momentum density p, and the
@@ -45,9 +54,8 @@ def test_maxwell_stress_relaxation_nonlinear():
     the Galerkin form of d(rho P_ij)/dt = -nu rho (P_ij - p delta_ij) with P the central
     second moment.  Checked on random f with every mode (Kmax = Lmax = 3) against the
     closed-form lambda_{0,2}: all other products of modes must cancel in these rows."""
-    km, lm = 3, 3
-    K, NQ = km + 1, (lm + 1) ** 2
-    op = dense.DenseOperator(km, lm, dense.conservation_zeroing(core.core(km, lm, 0.0), lm))
+    op = maxwell_33
+    K, NQ = op.K, op.NQ
     lam = _wcu_closed_form(0, 2)
     rng = np.random.default_rng(5)
     for _ in range(3):
@@ -58,6 +66,22 @@ def test_maxwell_stress_relaxation_nonlinear():
         Y2 = basis.real_sh_all(2, (p / np.linalg.norm(p))[None, :])[0, 4:9]
         expect = lam * (c[0, 0] * c[0, 4:9] - basis.radial_norm(0, 2) * (p @ p) * Y2)
         assert np.max(np.abs(Q[0, 4:9] - expect)) < 1e-13 * np.max(np.abs(expect))
+
+
+def test_maxwell_moment_closure_on_projected_maxwellians(maxwell_33):
+    """Maxwell molecules (§5.2): the collision rate of a degree-n moment depends only on
+    moments of degree <= n.  The projection of a drifting Maxwellian M_{U,T} (any U, T)
+    reproduces every moment of degree <= min(Lmax, 2 Kmax + 1) = 3 exactly, so the rows
+    2k + l <= 3 of Q vanish to rounding (Q(M, M) = 0), while the higher rows do not."""
+    op = maxwell_33
+    lq = np.array([basis.lm_of_q(q)[0] for q in range(op.NQ)])
+    deg = 2 * np.arange(op.K)[:, None] + lq[None, :]
+    for U, T in (([0.3, -0.2, 0.1], 1.4), ([0.0, 0.0, 0.5], 0.6)):
+        c = wi.maxwellian_coefficients(3, 3, np.array([0.8]), np.array([U]), np.array([T]))
+        Q = op.evaluate(c.reshape(1, -1)).reshape(op.K, op.NQ)
+        high = np.abs(Q[deg > 3]).max()
+        assert high > 1e-6
+        assert np.abs(Q[deg <= 3]).max() < 1e-11 * high
 
 
 def _wcu_closed_form(k, l):
