@@ -45,9 +45,10 @@ def maxwell_33():
     return dense.DenseOperator(3, 3, dense.conservation_zeroing(core.core(3, 3, 0.0), 3))
 
 
-def test_maxwell_stress_relaxation_nonlinear(maxwell_33):
+def test_maxwell_stress_and_heat_flux_relaxation_nonlinear(maxwell_33):
     """Maxwell molecules (§5.2): the traceless pressure tensor relaxes exactly at the first
-    l = 2 rate, whatever else f contains.  In the basis, phi_000 = 1 and phi_{0,(1,m)} =
+    l = 2 rate, whatever else f contains (and, at zero momentum, the heat flux at the first
+    l = 1 relaxation rate, 2/3 of it).  In the basis, phi_000 = 1 and phi_{0,(1,m)} =
     v_(y,z,x), so c_000 is the density and c_{0,(1,.)} the momentum density p, and the
     k = 0, l = 2 rows of the full nonlinear operator are
         Q_{0,(2,m)} = lambda_{0,2} (c_000 c_{0,(2,m)} - N_02 |p|^2 Y_2m(p / |p|)),
@@ -66,6 +67,16 @@ def test_maxwell_stress_relaxation_nonlinear(maxwell_33):
         Y2 = basis.real_sh_all(2, (p / np.linalg.norm(p))[None, :])[0, 4:9]
         expect = lam * (c[0, 0] * c[0, 4:9] - basis.radial_norm(0, 2) * (p @ p) * Y2)
         assert np.max(np.abs(Q[0, 4:9] - expect)) < 1e-13 * np.max(np.abs(expect))
+    # the heat flux (k = 1, l = 1 rows): at zero momentum it relaxes linearly at lambda_{1,1},
+    # two thirds of the stress rate (the Prandtl number 2/3 of Maxwell molecules)
+    lam11 = _wcu_closed_form(1, 1)
+    assert lam11 / lam == pytest.approx(2.0 / 3.0, rel=1e-13)
+    for _ in range(3):
+        c = 0.3 * rng.standard_normal((K, NQ))
+        c[0, 0], c[0, 1:4] = 1.1, 0.0
+        Q = op.evaluate(c.reshape(1, -1)).reshape(K, NQ)
+        expect = lam11 * c[0, 0] * c[1, 1:4]
+        assert np.max(np.abs(Q[1, 1:4] - expect)) < 1e-13 * np.max(np.abs(expect))
 
 
 def test_maxwell_moment_closure_on_projected_maxwellians(maxwell_33):
