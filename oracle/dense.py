@@ -78,6 +78,21 @@ class DenseOperator:
         f = np.asarray(f, dtype=np.float64).reshape(-1, self.N)
         return np.stack([np.einsum("ni,ni->n", f @ self.slice(a1), f) for a1 in a1_list], axis=1)
 
+    def evaluate_rows_with_terms(self, f, a1_list=None):
+        """Q[cell, a1] and T[cell, a1] = sum_{a2, a3} |C_{a1 a2 a3}| |f_a2| |f_a3| (the sum of
+        the absolute values of the terms of Q_a1: the scale that bounds the rounding error
+        of any summation order, against which cancellation in Q is measured) for the output
+        rows `a1_list` (default: all N)."""
+        f = np.asarray(f, dtype=np.float64).reshape(-1, self.N)
+        fa = np.abs(f)
+        rows = range(self.N) if a1_list is None else a1_list
+        Q, T = [], []
+        for a1 in rows:
+            S = self.slice(a1)
+            Q.append(np.einsum("ni,ni->n", f @ S, f))
+            T.append(np.einsum("ni,ni->n", fa @ np.abs(S), fa))
+        return np.stack(Q, axis=1), np.stack(T, axis=1)
+
     def linearized(self):
         """L[a1, a2] = C[a1, e0, a2] + C[a1, a2, e0] at c_000 = 1 (§5.3.1)."""
         L = np.empty((self.N, self.N))

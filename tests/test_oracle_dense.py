@@ -32,6 +32,43 @@ def test_dense_equals_literal_sum():
         assert np.allclose(Qd[i], Ql.reshape(-1), rtol=0, atol=1e-13)
 
 
+def test_absolute_terms_brute_force():
+    """T_a1 = sum |C_a1a2a3| |f_a2| |f_a3|, the cancellation scale the GPU parity tests guard
+    with: against the full tensor C = R * G assembled entry by entry from the oracle's Gaunt
+    tensor and summed term by term in pure Python; T >= |Q| everywhere, with equality
+    exactly where every term of a row has the same sign (here: |f| and |R| make every term
+    of a row share the sign of its Gaunt weights, so T = |Q| on rows whose weights agree)."""
+    km, lm = 1, 2
+    K, NQ = km + 1, (lm + 1) ** 2
+    R = wi.random_core(len(gaunt.channels(lm)), km, seed=15)
+    f = wi.random_cells(km, lm, 2, seed=16)
+    op = dense.DenseOperator(km, lm, R)
+    Q, T = op.evaluate_rows_with_terms(f.reshape(2, -1))
+    G = gaunt.gaunt_dense(lm)
+    cidx = gaunt.channel_index(lm)
+    lq = [basis.lm_of_q(q)[0] for q in range(NQ)]
+    for i in range(2):
+        fi = f[i]
+        for k1 in range(K):
+            for q1 in range(NQ):
+                t = 0.0
+                for k2 in range(K):
+                    for q2 in range(NQ):
+                        for k3 in range(K):
+                            for q3 in range(NQ):
+                                g = G[q1, q2, q3]
+                                if g == 0.0:
+                                    continue
+                                c = cidx[(lq[q1], lq[q2], lq[q3])]
+                                t += abs(R[c, k1, k2, k3] * g * fi[k2, q2] * fi[k3, q3])
+                assert abs(T[i, k1 * NQ + q1] - t) <= 1e-14 * max(t, 1e-300)
+    assert np.all(T >= np.abs(Q) * (1 - 1e-14))
+    # all terms of one sign: a core and cells made non-negative, rows whose Gaunt weights
+    # are all positive (the l1 = 0 rows: g = delta / sqrt(4 pi) >= 0) give T = Q
+    Qp, Tp = dense.DenseOperator(km, lm, np.abs(R)).evaluate_rows_with_terms(np.abs(f).reshape(2, -1), [0, NQ])
+    assert np.allclose(Qp, Tp, rtol=1e-14, atol=0)
+
+
 def _rotation(seed):
     rng = np.random.default_rng(seed)
     A = rng.standard_normal((3, 3))
