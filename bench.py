@@ -41,9 +41,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # 1987 MHz with full warps), x 152 SMs x 2 flops x 2070 MHz maximum clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel at the default workload
-# (K=L=12, 16384 cells), from a one-pass ncu capture of `bench.py --steps 1 --warmup 1
-# --precision rf32` (dram__bytes_read.sum 398.05 MB + dram__bytes_write.sum 325.89 MB).
-TRAFFIC_BYTES = {"rf32": 723.94e6}
+# (K=L=12, 16384 cells), from a one-pass ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the kernel as it is now; None until such a capture exists.
+TRAFFIC_BYTES = {"rf32": None}
+TRAFFIC_NOTE = "not captured for this kernel version"
 # arithmetic types of each path: FP64 reductions and projection, plus the radial products
 DTYPES = {"fp64": "f64", "bf16": "f64+bf16", "tf32": "f64+tf32", "rf32": "f64+f32"}
 
@@ -132,23 +133,28 @@ def sample_rows_of(rows):
     return N if rows is None or rows <= 0 else min(int(rows), N)
 
 
-def cpu_baseline(sample_cells, sample_rows=None, seed=3, with_angular_first=False):
+def cpu_baseline(sample_cells, sample_rows=None, seed=3, with_angular_first=False, R=None, f=None):
     """The oracle (dense FP64 CPU contraction) timed on a bounded sample of the workload:
     `sample_cells` cells and `sample_rows` of the N output rows (default all), scaled to
-    cells/s.  With `with_angular_first`, also the paper's factorised contraction in numpy
-    (a CPU comparison point, reported inside this object)."""
+    cells/s.  R, f: the workload's own core and cells (the sample is f's first cells); by
+    default a random stand-in core (the timing does not depend on the values) and fresh
+    two-Maxwellian cells.  Returns (line object, Q and the sums of |terms| of the sampled
+    cells and rows, the rows).  With `with_angular_first`, also the paper's factorised
+    contraction in numpy (a CPU comparison point, reported inside the object)."""
     import wef_inputs as wi
     from oracle import dense, gaunt
 
     K, NQ = KMAX + 1, (LMAX + 1) ** 2
     N = K * NQ
     sample_rows = sample_rows_of(sample_rows)
-    R = wi.random_core(len(gaunt.channels(LMAX)), KMAX, seed=11)  # timing does not depend on the values
-    f = wi.two_maxwellians(KMAX, LMAX, sample_cells, seed=seed).reshape(sample_cells, -1)
+    if R is None:
+        R = wi.random_core(len(gaunt.channels(LMAX)), KMAX, seed=11)
+    fs = (wi.two_maxwellians(KMAX, LMAX, sample_cells, seed=seed) if f is None else f[:sample_cells])
+    fs = np.asarray(fs).reshape(sample_cells, -1)
     op = dense.DenseOperator(KMAX, LMAX, dense.conservation_zeroing(R, LMAX))
-    rows = np.random.default_rng(seed).choice(N, sample_rows, replace=False)
+    rows = np.sort(np.random.default_rng(seed).choice(N, sample_rows, replace=False))
     t0 = time.perf_counter()
-    op.evaluate_rows(f, rows)
+    Qo, T = op.evaluate_rows_with_terms(fs, rows)
     dt = time.perf_counter() - t0
     value = sample_cells * (sample_rows / N) / dt
     out = {
@@ -157,8 +163,8 @@ def cpu_baseline(sample_cells, sample_rows=None, seed=3, with_angular_first=Fals
         "cores": os.cpu_count(),
         "cpu_model": cpu_model(),
         "kind": "oracle",
-        "sample": f"{sample_cells} cells x {sample_rows} of {N} output rows (dense C slices), {dt:.1f} s; "
-        f"numpy BLAS threads default (all {os.cpu_count()} host cores)",
+        "sample": f"{sample_cells} cells x {sample_rows} of {N} output rows (dense C slices, Q and its sums of "
+        f"|terms|), {dt:.1f} s; numpy BLAS threads default (all {os.cpu_count()} host cores)",
     }
     if with_angular_first:
         out["angular_first"] = cpu_angular_first()
@@ -166,7 +172,23 @@ def cpu_baseline(sample_cells, sample_rows=None, seed=3, with_angular_first=Fals
             out["angular_first_all_cores"] = cpu_angular_first_all_cores()
         except Exception as e:  # noqa: BLE001
             out["angular_first_all_cores"] = {"error": f"{type(e).__name__}: {e}"}
-    return out
+    return out, (Qo, T, rows)
+
+
+ERROR_EPS = 2.0 ** -10  # cancellation floor of the per-cell error, relative to the sums of |terms|
+
+
+def error_vs_oracle(Q, Qo, T):
+    """Per-cell error of Q [cells, rows] against the oracle: max_a |Q - Qo| over the cell's
+    rows divided by max(max_a |Qo|, ERROR_EPS * max_a T) (the infinity norm of the cell,
+    guarded against cancellation), reported as max and median over the cells, with the
+    plain per-cell relative error beside it."""
+    d = np.max(np.abs(Q - Qo), axis=1)
+    qn = np.max(np.abs(Qo), axis=1)
+    g = d / np.maximum(np.maximum(qn, ERROR_EPS * np.max(T, axis=1)), 1e-300)
+    r = d / np.maximum(qn, 1e-300)
+    return {"max": float(np.max(g)), "median": float(np.median(g)), "plain_rel_max": float(np.max(r)),
+            "plain_rel_median": float(np.median(r))}
 
 
 def cpu_angular_first(sample_cells=32, seed=3):
@@ -305,7 +327,7 @@ def run_reference(args, rank, world):
     for _ in range(args.warmup):
         cpu_baseline(args.cpu_sample_cells, rows)
     t0 = time.perf_counter()
-    samples = [cpu_baseline(args.cpu_sample_cells, rows) for _ in range(max(args.steps, 1))]
+    samples = [cpu_baseline(args.cpu_sample_cells, rows)[0] for _ in range(max(args.steps, 1))]
     dt = time.perf_counter() - t0
     cells_per_step = args.cpu_sample_cells * sample_rows_of(rows) / ((KMAX + 1) * (LMAX + 1) ** 2)
     value = cells_per_step * len(samples) / dt
@@ -540,9 +562,12 @@ def bench_ragged(args, W, torch, dev, world, ncells=32768, seed=4):
                                        "streams in one CUDA graph"})
 
 
-def bench_serve(args, W, torch, dev, world):
-    """Poisson stream of requests (1-4096 cells, Kmax=Lmax in {8,10,12,16}, hard spheres),
-    continuous batching with memory admission; rate = 0.7 x measured capacity."""
+def serving_leg(args, W, torch, dev, duration):
+    """Configuration 5: a seeded Poisson stream of requests (1-4096 cells, Kmax=Lmax drawn from
+    {8,10,12,16}, hard-sphere-sized operators) served by the continuous-batching loop at 0.7x
+    the measured capacity for `duration` seconds of arrivals.  Requests read their cells from
+    per-shape pinned pools and receive their Q in per-shape pinned result buffers (set up
+    before serving); latency runs from arrival to the result in host memory."""
     import wef_inputs as wi
     from paper_2605_28475_gb300 import serve
 
@@ -553,10 +578,11 @@ def bench_serve(args, W, torch, dev, world):
         op = W.Operator(km, lm, 1.0)
         op.upload_core(op.build_core(device=True) if real else wi.random_core(op.n_channels, km, seed=300 + i))
         ops[(km, lm)] = op
-    # capacity: full-batch throughput per shape at the serving precision
     prec = W.PRECISIONS[args.precision]
     st = torch.cuda.current_stream(dev)
-    cap = {}
+    max_cells = 4096
+    # capacity: full-batch throughput per shape at the serving precision
+    cap, pools = {}, {}
     for sh, op in ops.items():
         n = 2048
         f = torch.from_numpy(wi.random_cells(sh[0], sh[1], n, seed=1)).to(dev)
@@ -565,25 +591,43 @@ def bench_serve(args, W, torch, dev, world):
         step = lambda: W.wef_evaluate(op.h, f.data_ptr(), q.data_ptr(), n, prec, ws.data_ptr(), ws.numel(), st.cuda_stream)  # noqa: E731,B023
         ms = _time_steps(step, 3, 1, st, torch)
         cap[sh] = n / (ms / 1e3)  # cells/s at this shape
-    max_cells = 4096
+        pools[sh] = (torch.from_numpy(wi.random_cells(sh[0], sh[1], max_cells, seed=2)).pin_memory(),
+                     torch.empty(max_cells, sh[0] + 1, (sh[1] + 1) ** 2, dtype=torch.float64).pin_memory())
     # mean service time of a request (log-uniform size, uniform shape) at full-batch speed
     sizes = np.exp(np.linspace(0, np.log(max_cells), 2001))
     mean_cells = float(np.mean(sizes))
     mean_service = float(np.mean([mean_cells / cap[sh] for sh in shapes]))
     rate = 0.7 / mean_service
-    reqs = serve.poisson_requests(rate, args.duration, shapes, max_cells, seed=5,
-                                  make_cells=lambda sh, n, s: wi.random_cells(sh[0], sh[1], n, seed=s))
+    reqs = serve.poisson_requests(rate, duration, shapes, max_cells, seed=5,
+                                  make_cells=lambda sh, n, s: pools[sh][0][:n])
+    for r in reqs:
+        r.out = pools[r.shape][1][:r.f.shape[0]]
+    cost = {sh: 1.0 / c for sh, c in cap.items()}
     # batches capped at ~50 ms of estimated GPU time so that small requests do not queue
     # behind one huge batch (a single larger request still goes alone)
     srv = serve.Server(ops, arena_bytes=24 << 30, nslots=8, precision=args.precision, device=str(dev),
-                       cost_per_cell={sh: 1.0 / c for sh, c in cap.items()}, max_batch_s=0.05)
-    res = serve.run(srv, reqs)
-    dtype = DTYPES[args.precision]
-    return _line("serve: p50/p99 latency and cells/s", res["cells_per_s"], "cells/s", None, args, world, dtype,
-                 f"Poisson arrivals at 0.7x capacity ({rate:.1f} req/s) for {args.duration:.0f} s; sizes log-uniform "
-                 f"1-{max_cells} cells; Kmax=Lmax in {{8,10,12,16}}; 8 stream slots; 24 GiB admission arena; "
-                 f"batches capped at 50 ms of estimated GPU time",
-                 serving=res, capacity_cells_per_s={f"{k[0]}x{k[1]}": v for k, v in cap.items()})
+                       cost_per_cell=cost, max_batch_s=0.05)
+    with ClockSampler(dev.index or 0) as clk:
+        res = serve.run(srv, reqs, service_s=lambda r: r.f.shape[0] * cost[r.shape])
+    res["clocks"] = clk.summary()
+    res.update(rate_req_per_s=rate, duration_s=duration, ragged_batches=srv.ragged,
+               capacity_cells_per_s={f"{k[0]}x{k[1]}": v for k, v in cap.items()},
+               note=(f"Poisson arrivals at 0.7x capacity ({rate:.1f} req/s) for {duration:.0f} s; sizes log-uniform "
+                     f"1-{max_cells} cells; Kmax=Lmax in {{8,10,12,16}}; 8 stream slots; 24 GiB admission arena; "
+                     f"batches {'mixing every shape (wef_evaluate_ragged)' if srv.ragged else 'of one shape'}, capped "
+                     f"at 50 ms of estimated GPU time; latency = arrival to Q in pinned host memory; slowdown = "
+                     f"latency / the request's own service time at full-batch speed; cores "
+                     + ("from the library quadrature" if real else "random stand-ins (timing does not depend on values)")))
+    for op in ops.values():
+        op.close()
+    return res
+
+
+def bench_serve(args, W, torch, dev, world):
+    """Serving alone (configuration 5), as its own JSON line."""
+    res = serving_leg(args, W, torch, dev, args.duration)
+    return _line("serve: p50/p99 latency and cells/s", res["cells_per_s"], "cells/s", None, args, world,
+                 DTYPES[args.precision], res["note"], serving=res)
 
 
 def main():
@@ -682,8 +726,15 @@ def main():
 
     variants = {}
     order = [p for p in ("fp64", "bf16", "tf32", "rf32") if p != args.precision] + [args.precision]
+    nsample = min(args.cpu_sample_cells, ncells)
+    q_sample, invariant_max = {}, {}
+    qv = q.view(ncells, KMAX + 1, (LMAX + 1) ** 2)
     for pr in order:
         variants[pr] = measure(pr, with_clocks=(pr == args.precision))
+        # the result of the last timed step: the cells the oracle checks, and the largest
+        # |Q| over every cell's mass, momentum and energy outputs (exact zeros by Sec. 4.4)
+        q_sample[pr] = qv[:nsample].reshape(nsample, -1).cpu().numpy()
+        invariant_max[pr] = max(float(qv[:, 0, 0:4].abs().max()), float(qv[:, 1, 0].abs().max()))
     head = variants[args.precision]
     step = head["step"]
     # end to end through the C ABI with host buffers: wef_evaluate_host streams pinned f to
@@ -709,6 +760,10 @@ def main():
     a1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = a0.elapsed_time(a1) / args.steps
+    # configuration 5 (serving), timed after the headline legs
+    serving = None
+    if world == 1 and os.environ.get("WEF_BENCH_NO_SERVE") != "1" and args.duration > 0:
+        serving = serving_leg(args, W, torch, dev, args.duration)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -747,9 +802,8 @@ def main():
             "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": TRAFFIC_BYTES.get(args.precision) if (ncells == NCELLS and KMAX == 12) else None,
-            "traffic_note": ("DRAM bytes per launch (one-pass ncu capture at 16384 cells); algorithmic: FP32 tiles "
-                             "in + FP64 Q out = 432 MB. Captured before q2 groups were paired by shared q3 "
-                             "(same kernel code, its program then had 32707 instead of 31613 union entries)"),
+            "traffic_note": "DRAM bytes per launch (one-pass ncu capture at 16384 cells); algorithmic: FP32 tiles "
+                            "in + FP64 Q out = 432 MB; " + TRAFFIC_NOTE,
             "fp64_flops_per_cell": head["fp64_flops_per_cell"],
             "radial_flops_per_cell": head["radial_flops_per_cell"],
             "radial_note": "low-precision radial flops: tensor-core (bf16, tf32) or FP32 CUDA-core (rf32)",
@@ -770,8 +824,23 @@ def main():
         "gpu_launches": 2 * args.steps,
         "clocks": head["clocks"],
     }
+    if serving is not None:
+        line["serving"] = {k: serving[k] for k in ("p50_ms", "p99_ms", "cells_per_s", "completed", "rejected",
+                                                    "requests", "batches", "slowdown_p50", "slowdown_p99",
+                                                    "mean_queue_ms", "wall_s", "clocks", "note") if k in serving}
     if world == 1 and os.environ.get("WEF_BENCH_NO_CPU") != "1":
-        line["cpu_baseline"] = cpu_baseline(args.cpu_sample_cells, args.cpu_sample_rows, with_angular_first=True)
+        cb, (Qo, T, rows) = cpu_baseline(nsample, args.cpu_sample_rows, with_angular_first=True, R=R, f=f_host)
+        line["cpu_baseline"] = cb
+        line["error_vs_oracle"] = {
+            "metric": f"per cell: max over its output rows of |Q - Q_oracle| / max(max |Q_oracle|, 2^-10 x max sum "
+                      f"of |terms|); max and median over {nsample} cells (the oracle's sample: the batch's first "
+                      f"cells, {len(rows)} output rows each, the hard-sphere core of this run); invariant_max_abs = "
+                      f"largest |Q| of the mass, momentum and energy outputs over all {ncells} cells",
+            **{pr: {**error_vs_oracle(q_sample[pr][:, rows], Qo, T), "invariant_max_abs": invariant_max[pr]}
+               for pr in order},
+        }
+    else:
+        line["error_vs_oracle"] = {pr: {"invariant_max_abs": invariant_max[pr]} for pr in order}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

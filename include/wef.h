@@ -82,8 +82,9 @@ typedef enum {
  */
 wef_status wef_create(int kmax, int lmax, double gamma, wef_op* out);
 
-/* Sizes of the operator: N = K*NQ per cell, number of channels N_T, Gaunt
- * nonzeros N_G, and the core length N_T*K^3 (doubles).  Any out pointer may be NULL.
+/* Sizes of the operator: N = K*NQ per cell (Sec. 2.2: K radial functions times NQ real
+ * harmonics), number of channels N_T (Sec. 4.6), Gaunt nonzeros N_G (Sec. 4.2, Table 6),
+ * and the core length N_T*K^3 (doubles; Sec. 4.3).  Any out pointer may be NULL.
  * Errors: WEF_EINVAL (op NULL). */
 wef_status wef_sizes(wef_op op, int64_t* n_per_cell, int64_t* n_channels, int64_t* n_gaunt, int64_t* core_len);
 
@@ -171,6 +172,39 @@ wef_status wef_plan_autotune(wef_plan plan, const double* f_dev, double* q_dev, 
 /* Synchronous check of the plan's device status word (see wef_device_status). */
 wef_status wef_plan_status(wef_plan plan, int reset);
 wef_status wef_plan_destroy(wef_plan plan);
+
+/*
+ * wef_evaluate_ragged - Q = Q(f, f) for a batch mixing cells of several operators, each cell
+ * anywhere in f and q: the bilinear form of Sec. 2.3, Q_a = sum_bc C_abc f_b f_c, evaluated
+ * per cell by the contraction of Sec. 4.5 that `prec` selects (WEF_RADIAL_FP32: the Sec.
+ * 4.5.3 ordering with FP32 radial stages and an FP64 Gaunt reduction; WEF_FP64: the
+ * Sec. 4.5.4 angular-first contraction in FP64), with the Sec. 4.4 projection.
+ *   ops[0..nops-1]: 1 <= nops <= WEF_RAGGED_MAX_OPS operators with uploaded cores, all on the
+ *     current device (host array of handles; the operators must outlive the queued work).
+ *   shape_id_dev[i] (device, int32, ncells entries): the operator of cell i, an index into
+ *     ops; cells with an index outside [0, nops) are skipped (their Q is not written).
+ *   offset_dev[i] (device, int64): where cell i's K*NQ values start, in doubles from f_dev;
+ *     its Q is written at the same offset from q_dev (layout k*NQ + q of its operator).
+ *     Cells must not overlap in q_dev; f and q may not alias.
+ *   workspace: device, 256-byte aligned, at least wef_ragged_workspace_size bytes (which
+ *     depends only on the operators, ncells and prec); scratch, overwritten.
+ * Asynchronous on `stream`, allocates no device memory, reads nothing back to the host: the
+ * batch's composition is worked out on the device (per-operator counts, cell lists and
+ * 32-cell tiles, set up by kernels on `stream`), then each operator's contraction runs over
+ * its own tiles on one of a few streams forked from `stream` and joined back to it.  Each
+ * cell's result is bitwise the one wef_evaluate gives for that cell at the same precision.
+ * The forked streams are created by the first call on each device (make that call before
+ * any stream capture); calls from several host threads take turns queueing their work.
+ * Errors (checked before anything is queued): WEF_EINVAL (NULL argument, nops out of range,
+ * a precision other than the two above, ncells < 0 or too large, workspace unaligned or too
+ * small, an operator on another device), WEF_ENOCORE; WEF_ECUDA if a launch fails.
+ * ncells == 0 is a no-op.
+ */
+#define WEF_RAGGED_MAX_OPS 32
+wef_status wef_ragged_workspace_size(const wef_op* ops, int nops, int64_t ncells, wef_precision prec, int64_t* bytes);
+wef_status wef_evaluate_ragged(const wef_op* ops, int nops, const int32_t* shape_id_dev, const int64_t* offset_dev,
+                               const double* f_dev, double* q_dev, int64_t ncells, wef_precision prec,
+                               void* workspace, int64_t ws_bytes, void* stream);
 
 /*
  * Evaluation from host memory: the same Q(f, f) for f and Q in host memory (pinned for
@@ -294,7 +328,10 @@ wef_status wef_device_status(wef_op op, int reset);
  *     must fit the scratch (928 cells at Kmax = Lmax = 12); larger batches are
  *     rejected with WEF_EINVAL and a message giving the limit.
  *   - The first call on each device looks up the scratch's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current), which is also when CUDA loads the library module holding
+ *     the array, making its 16 MiB resident with an implicit device synchronisation;
+ *     make that first call at set-up, before any stream capture.  Later calls
+ *     allocate nothing.
  *   - All calls on a device share the one scratch array, which keeps the last
  *     call's contents: calls that overlap on the GPU (other streams, other
  *     threads) race and must be ordered by the caller.

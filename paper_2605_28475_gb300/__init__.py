@@ -57,6 +57,9 @@ def lib():
             "wef_plan_status": ([vp, ctypes.c_int], ctypes.c_int),
             "wef_plan_destroy": ([vp], ctypes.c_int),
             "wef_evaluate_noalloc": ([vp, vp, vp, i64, vp], ctypes.c_int),
+            "wef_ragged_workspace_size": ([ctypes.POINTER(vp), ctypes.c_int, i64, ctypes.c_int, i64p], ctypes.c_int),
+            "wef_evaluate_ragged": ([ctypes.POINTER(vp), ctypes.c_int, vp, vp, vp, vp, i64, ctypes.c_int, vp, i64, vp],
+                                    ctypes.c_int),
             "wef_integrate_workspace_size": ([vp, i64, ctypes.c_int, i64p], ctypes.c_int),
             "wef_integrate": ([vp, vp, i64, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, i64, vp], ctypes.c_int),
             "wef_linearized_apply": ([vp, vp, vp, vp, i64, ctypes.c_int, vp, i64, vp], ctypes.c_int),
@@ -125,6 +128,21 @@ def wef_evaluate(op, f_ptr, q_ptr, ncells, prec, ws_ptr, ws_bytes, stream_ptr):
 
 def wef_evaluate_noalloc(op, f_ptr, q_ptr, ncells, stream_ptr):
     _check(lib().wef_evaluate_noalloc(op, f_ptr, q_ptr, int(ncells), stream_ptr))
+
+
+def _op_array(ops):
+    return (ctypes.c_void_p * len(ops))(*[o.value if isinstance(o, ctypes.c_void_p) else o for o in ops])
+
+
+def wef_ragged_workspace_size(ops, ncells, prec=WEF_RADIAL_FP32):
+    b = ctypes.c_int64()
+    _check(lib().wef_ragged_workspace_size(_op_array(ops), len(ops), int(ncells), int(prec), ctypes.byref(b)))
+    return b.value
+
+
+def wef_evaluate_ragged(ops, shape_id_ptr, offset_ptr, f_ptr, q_ptr, ncells, prec, ws_ptr, ws_bytes, stream_ptr):
+    _check(lib().wef_evaluate_ragged(_op_array(ops), len(ops), shape_id_ptr, offset_ptr, f_ptr, q_ptr, int(ncells),
+                                     int(prec), ws_ptr, int(ws_bytes), stream_ptr))
 
 
 def wef_core_build(op, pad_rad=20, pad_ang=20):

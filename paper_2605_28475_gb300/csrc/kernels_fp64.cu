@@ -44,13 +44,20 @@ __global__ void __launch_bounds__(32 * K) fp64_kernel(const double* __restrict__
                                                       const int4* __restrict__ groups, const double2* __restrict__ gw,
                                                       const int32_t* __restrict__ task_off,
                                                       const int32_t* __restrict__ chunks,
-                                                      const double* __restrict__ R64) {
+                                                      const double* __restrict__ R64, RaggedView rv) {
   extern __shared__ double red[];  // [k3][k1][32]
   const int k3 = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tile = blockIdx.x;
+  if (rv.count) {  // one shape of a ragged batch: the grid is an upper bound of its tiles
+    ncells = *rv.count;
+    if (tile * 32 >= ncells) return;
+    ftile += *rv.tile_off;
+    rv.cells += *rv.cells_off;
+  }
   const int t0 = chunks[blockIdx.y], t1 = chunks[blockIdx.y + 1];
   const double* ft = ftile + tile * (int64_t)NQ * K * 32 + lane;
   const int64_t cell = tile * 32 + lane;
+  double* qcell = qout + (cell < ncells && rv.cells ? rv.cells[cell] : cell * (int64_t)K * NQ);
   for (int t = t0; t < t1; ++t) {
     const int32_t* p = prog + task_off[t];
     const int q1 = __ldg(p);
@@ -85,22 +92,25 @@ __global__ void __launch_bounds__(32 * K) fp64_kernel(const double* __restrict__
       for (int j = 0; j < K; ++j) s += red[(j * K + k1) * 32 + lane];
       // conservation projection: mass (k=0,l=0), momentum (k=0,l=1), energy (k=1,l=0)
       if ((k1 == 0 && q1 < 4) || (k1 == 1 && q1 == 0)) s = 0.0;
-      if (cell < ncells) qout[cell * (int64_t)K * NQ + (int64_t)k1 * NQ + q1] = s;
+      if (cell < ncells) qcell[(int64_t)k1 * NQ + q1] = s;
     }
     __syncthreads();
   }
 }
 
+// ncells: the cells of a one-shape call, or (rv.count set) an upper bound of the shape's
+// cells in a ragged batch, which sizes the grid.
 template <int K>
 cudaError_t launch_fp64_k(const double* ftile, double* q, int64_t ncells, int NQ, const DevProgram& p,
-                          const int32_t* chunks, int nchunks, const double* R64, cudaStream_t s) {
+                          const int32_t* chunks, int nchunks, const double* R64, cudaStream_t s,
+                          const RaggedView& rv) {
   const int64_t ntiles = (ncells + 31) / 32;
   const size_t smem = (size_t)K * K * 32 * sizeof(double);
   static std::atomic<size_t> attr[kMaxDevices];
   cudaError_t e = smem_opt_in(fp64_kernel<K>, smem, attr);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)ntiles, (unsigned)nchunks);
-  fp64_kernel<K><<<grid, 32 * K, smem, s>>>(ftile, q, ncells, NQ, p.prog, p.groups, p.gw, p.task_off, chunks, R64);
+  fp64_kernel<K><<<grid, 32 * K, smem, s>>>(ftile, q, ncells, NQ, p.prog, p.groups, p.gw, p.task_off, chunks, R64, rv);
   return cudaGetLastError();
 }
 
@@ -115,11 +125,11 @@ cudaError_t launch_tile_f(const double* f, double* ftile, int64_t ncells, int K,
 }
 
 cudaError_t launch_fp64(int K, const double* ftile, double* q, int64_t ncells, int NQ, const DevProgram& p,
-                        const int32_t* chunks, int nchunks, const double* R64, cudaStream_t s) {
+                        const int32_t* chunks, int nchunks, const double* R64, cudaStream_t s, const RaggedView& rv) {
   switch (K) {
 #define WEF_CASE(k) \
   case k:           \
-    return launch_fp64_k<k>(ftile, q, ncells, NQ, p, chunks, nchunks, R64, s);
+    return launch_fp64_k<k>(ftile, q, ncells, NQ, p, chunks, nchunks, R64, s, rv);
     WEF_CASE(1) WEF_CASE(2) WEF_CASE(3) WEF_CASE(4) WEF_CASE(5) WEF_CASE(6) WEF_CASE(7) WEF_CASE(8) WEF_CASE(9)
     WEF_CASE(10) WEF_CASE(11) WEF_CASE(12) WEF_CASE(13) WEF_CASE(14) WEF_CASE(15) WEF_CASE(16) WEF_CASE(17)
 #undef WEF_CASE

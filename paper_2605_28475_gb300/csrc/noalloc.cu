@@ -33,6 +33,7 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 extern "C" wef_status wef_evaluate_noalloc(wef_op op, const double* f_dev, double* q_dev, int64_t ncells,
                                            void* stream) {
+  return wef::guarded("wef_evaluate_noalloc", [&]() -> wef_status {
   if (!op) return wef::set_error(WEF_EINVAL, "wef_evaluate_noalloc: op is NULL");
   if (ncells < 0) return wef::set_error(WEF_EINVAL, "wef_evaluate_noalloc: ncells < 0");
   int64_t need = 0;
@@ -54,7 +55,9 @@ extern "C" wef_status wef_evaluate_noalloc(wef_op op, const double* f_dev, doubl
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_addr[dev]) {
-      // set-up, once per device, with that device current
+      // set-up, once per device, with that device current.  This is also where CUDA's lazy
+      // module loading brings in the module holding the array (its 16 MiB become resident,
+      // with an implicit device synchronisation): a reason more to make the first call at set-up.
       void* p = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p)
@@ -66,4 +69,5 @@ extern "C" wef_status wef_evaluate_noalloc(wef_op op, const double* f_dev, doubl
   // The re-tiling kernel overwrites every scratch byte it later reads (tail cells
   // are written as zeros), so nothing needs clearing between calls.
   return wef_evaluate(op, f_dev, q_dev, ncells, WEF_FP64, scratch, (int64_t)WEF_NOALLOC_SCRATCH_BYTES, stream);
+  });
 }

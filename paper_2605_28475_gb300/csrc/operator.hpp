@@ -30,7 +30,7 @@ struct wef_operator {
   double* d_R64 = nullptr;      // symmetrised core [sc][k3][k1][k2]
   uint8_t* d_Bbf16 = nullptr;   // packed MMA B tiles, BF16
   uint8_t* d_Btf32 = nullptr;   // packed MMA B tiles, TF32
-  float* d_R32 = nullptr;       // symmetrised core, FP32 [sc][k1][k3][KP4] (radial-first path)
+  float* d_R32 = nullptr;       // symmetrised core, FP32 [sc][k1][k2][KP4] (radial-first path)
   bool has_core = false;
   // tracing
   cudaEvent_t trace_start = nullptr, trace_stop = nullptr;

@@ -13,23 +13,29 @@
 namespace wef {
 namespace rfk {
 
-// Exact FP32 -> FP64 with 32-bit integer instructions (keeps the FP64 pipe free).
-// FP32 subnormals flush to zero (below 1.2e-38).
-__device__ __forceinline__ double f2d_exact(float x) {
+// FP32 -> FP64 with 32-bit integer instructions (keeps the FP64 pipe free), scaled by
+// 2^-896: moving the FP32 exponent and mantissa fields into the FP64 positions without
+// re-biasing the exponent gives, for every finite x (zeros and subnormals included),
+// exactly x * 2^-896 (FP32 exponent field e -> 2^(e-1023) instead of 2^(e-127); an FP32
+// subnormal lands on the FP64 subnormal with the same ratio).  The radial-first program
+// stores its Gaunt weights premultiplied by 2^896 (exact, |g| < 1), so the FP64 product
+// g' * x' equals g * x exactly and the FMA rounds as it would on g * (double)x.
+// Inf and NaN keep their meaning (rare branch).
+__device__ __forceinline__ double f2d_scaled(float x) {
   const uint32_t u = __float_as_uint(x);
-  const uint32_t sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
-  uint32_t hi, lo;
-  if (e == 0u) {
-    hi = sign;
-    lo = 0u;
-  } else if (e == 0xFFu) {
-    hi = sign | 0x7FF00000u | (m >> 3);
-    lo = m << 29;
-  } else {
-    hi = sign | ((e + 896u) << 20) | (m >> 3);
-    lo = m << 29;
-  }
-  return __hiloint2double((int)hi, (int)lo);
+  if ((u & 0x7F800000u) == 0x7F800000u)
+    return __hiloint2double((int)((u & 0x80000000u) | 0x7FF00000u | ((u & 0x7FFFFFu) >> 3)), (int)(u << 29));
+  const uint32_t hi = (uint32_t)((int32_t)u >> 3) & 0x8FFFFFFFu;  // sign, then e and the top of m
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// c + a * b on a pair of FP32 values (two independent FMAs, each rounded once).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+#ifdef WEF_RF_SCALAR_FMA
+  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#else
+  return __ffma2_rn(a, b, c);
+#endif
 }
 
 // The shell's FP64 accumulators Q[k1 = warp][q1 offset m][cell = lane], in shared memory
@@ -90,15 +96,18 @@ struct AccTmem {
 // Thread mapping: lane = cell, warp = radial row k1 (K warps per CTA).  Each warp walks the
 // program on its own: per channel, per block of J q2 groups, stage 1 for the J groups
 // (core rows as float4, reused by the J groups), then the union of the block's q3: f[:, q3]
-// is loaded once and serves every q2 of the block it pairs with.
+// is loaded once and serves every q2 of the block it pairs with.  Both radial stages run
+// as packed FP32x2 FMAs over k3 pairs: A is kept as KH float2 per q2 group, and each
+// packed FMA advances the even-k3 and the odd-k3 partial sums of one dot product (the
+// same two chains, in the same order, as scalar code with two accumulators).
 template <int K>
 struct RfCfg {
-  static constexpr int KP4 = (K + 3) / 4 * 4;  // padded k2 (float4 core rows)
+  static constexpr int KH = (K + 1) / 2;      // k3 pairs
+  static constexpr int KP4 = (K + 3) / 4 * 4;  // padded k3 (float4 core rows)
   static constexpr int J = rf_group_width(K, false);  // q2 groups per block, shared-memory variant
-  // Registers per thread that let two CTAs share an SM: each of the 4 sub-partitions has
-  // 16384 registers and takes ceil(2 K / 4) of the two CTAs' warps.
   // CTAs per SM the register budget is sized for: about 32-36 resident warps where the
-  // accumulators of a Kmax = Lmax shell let that many CTAs share the shared memory
+  // accumulators of a Kmax = Lmax shell let that many CTAs share the shared memory.  Each of
+  // the 4 sub-partitions has 16384 registers and takes ceil(CTAS K / 4) of the warps.
   static constexpr int CTAS = rf_ctas_per_sm(K);
   static constexpr int WARPS_PER_SMSP = (CTAS * K + 3) / 4;
   static constexpr int MAXREG_RAW = 16384 / (32 * WARPS_PER_SMSP) / 8 * 8;
@@ -115,11 +124,18 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(TMEM ? RfCfg<K>::MAXREG_1C
               const int4* __restrict__ tasks, const int4* __restrict__ chans, const int4* __restrict__ blocks,
               const int4* __restrict__ uents, const double2* __restrict__ pw,
               const int32_t* __restrict__ order, int ntasks, const float* __restrict__ R32, int* __restrict__ queue,
-              int64_t group, int n1max, uint32_t tcols) {
+              int64_t group, int n1max, uint32_t tcols, RaggedView rv) {
   using Cfg = RfCfg<K>;
-  constexpr int J = rf_group_width(K, TMEM), KP4 = Cfg::KP4, R4 = KP4 / 4, S = K * 32;
+  constexpr int J = rf_group_width(K, TMEM), KH = Cfg::KH, R4 = Cfg::KP4 / 4, S = K * 32;
   __shared__ int item_s;
   const int k1 = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (rv.count) {  // one shape of a ragged batch: its size and tiles come from the device
+    ncells = *rv.count;
+    ntiles = (ncells + 31) / 32;
+    ftile += *rv.tile_off;
+    rv.cells += *rv.cells_off;
+    if (group > ntiles) group = ntiles > 0 ? ntiles : 1;
+  }
   const int64_t nitems = ntiles * ntasks;
   // Accumulators in tensor memory: warp k1 uses lane quadrant k1 % 4 and columns from
   // (k1 / 4) * 2 * n1max on; one allocation for the CTA's lifetime.  Otherwise in
@@ -172,62 +188,59 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(TMEM ? RfCfg<K>::MAXREG_1C
     acc.zero(T.y, S);
     for (int ch = T.z; ch < T.z + T.w; ++ch) {
       const int4 C = __ldg(chans + ch);  // sc, blk_start, nblk
-      const float4* Ra = reinterpret_cast<const float4*>(R32 + ((int64_t)C.x * K + k1) * K * KP4);  // [k3][k2]
+      const float4* Ra = reinterpret_cast<const float4*>(R32 + ((int64_t)C.x * K + k1) * K * Cfg::KP4);  // [k2][k3]
       for (int b = C.y; b < C.y + C.z; ++b) {
         const int4 B0 = __ldg(blocks + 2 * b), B1 = __ldg(blocks + 2 * b + 1);  // {nj, u_start, nu}, q2s
-        const int nj = B0.x;
-        const int q2v[4] = {B1.x, B1.y, B1.z, B1.w};
-        float fq[J][KP4];
+        const int q2v[4] = {B1.x, B1.y, B1.z, B1.w};  // entries j >= nj are 0 (a valid row)
+        // stage 1: A[j][k3] = sum_k2 Rt[k1][k2][k3] f[k2][q2_j], k2 ascending, one chain per (j, k3)
+        float2 A2[J][KH];
 #pragma unroll
         for (int j = 0; j < J; ++j)
 #pragma unroll
-          for (int k2 = 0; k2 < KP4; ++k2) fq[j][k2] = (j < nj && k2 < K) ? __ldg(ft + (q2v[j] * K + k2) * 32) : 0.0f;
-        // stage 1: A[j][k3] = sum_k2 Rt[k1][k2][k3] f[k2][q2_j]
-        float A[J][K];
+          for (int i = 0; i < KH; ++i) A2[j][i] = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int k3 = 0; k3 < K; ++k3) {
-          float a[J];
+        for (int k2 = 0; k2 < K; ++k2) {
+          float2 fd[J];
 #pragma unroll
-          for (int j = 0; j < J; ++j) a[j] = 0.0f;
-#pragma unroll
-          for (int c = 0; c < R4; ++c) {
-            const float4 r = __ldg(Ra + k3 * R4 + c);
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-              a[j] = fmaf(r.x, fq[j][4 * c], a[j]);
-              a[j] = fmaf(r.y, fq[j][4 * c + 1], a[j]);
-              a[j] = fmaf(r.z, fq[j][4 * c + 2], a[j]);
-              a[j] = fmaf(r.w, fq[j][4 * c + 3], a[j]);
-            }
+          for (int j = 0; j < J; ++j) {
+            const float v = __ldg(ft + (q2v[j] * K + k2) * 32);
+            fd[j] = make_float2(v, v);
           }
 #pragma unroll
-          for (int j = 0; j < J; ++j) A[j][k3] = a[j];
+          for (int c = 0; c < R4; ++c) {
+            const float4 r = __ldg(Ra + k2 * R4 + c);
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+              if (2 * c < KH) A2[j][2 * c] = fma2(make_float2(r.x, r.y), fd[j], A2[j][2 * c]);
+              if (2 * c + 1 < KH) A2[j][2 * c + 1] = fma2(make_float2(r.z, r.w), fd[j], A2[j][2 * c + 1]);
+            }
+          }
         }
         // stage 2 + FP64 reduction over the union of the block's q3
+        // the next union record is loaded one entry ahead, so that the loads of f[:, q3]
+        // do not wait for their own record
+        int4 Un = __ldg(uents + B0.y);
         for (int u = B0.y; u < B0.y + B0.z; ++u) {
-          const int4 U = __ldg(uents + u);  // q3 | mask << 16, pair_start, packed targets
+          const int4 U = Un;  // q3 | mask << 16, pair_start, packed targets
+          if (u + 1 < B0.y + B0.z) Un = __ldg(uents + u + 1);
           const int q3 = U.x & 0xFFFF, mask = U.x >> 16;
           const float* f3 = ft + q3 * K * 32;
-          // J = 1 (large K, tight registers): consume f[:, q3] as it arrives
-          float x[J > 1 ? K : 1];
-          if constexpr (J > 1) {
+          float2 xp[KH];
 #pragma unroll
-            for (int k3 = 0; k3 < K; ++k3) x[k3] = __ldg(f3 + k3 * 32);
+          for (int i = 0; i < KH; ++i) {
+            xp[i].x = __ldg(f3 + (2 * i) * 32);
+            xp[i].y = 2 * i + 1 < K ? __ldg(f3 + (2 * i + 1) * 32) : 0.0f;
           }
           int p = U.y;
 #pragma unroll
           for (int j = 0; j < J; ++j) {
             if (!((mask >> j) & 1)) continue;
-            float b0 = 0.0f, b1 = 0.0f;
+            float2 b = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int k3 = 0; k3 < K; ++k3) {
-              const float xv = J > 1 ? x[J > 1 ? k3 : 0] : __ldg(f3 + k3 * 32);
-              if (k3 & 1) b1 = fmaf(A[j][k3], xv, b1);
-              else b0 = fmaf(A[j][k3], xv, b0);
-            }
-            const double Bv = f2d_exact(b0 + b1);
+            for (int i = 0; i < KH; ++i) b = fma2(A2[j][i], xp[i], b);
+            const double Bv = f2d_scaled(b.x + b.y);
             const uint32_t T = ((uint32_t)(j < 2 ? U.z : U.w) >> (16 * (j & 1))) & 0xFFFFu;  // targets
-            const double2 W = __ldg(pw + p);
+            const double2 W = __ldg(pw + p);  // Gaunt weights x 2^896
             ++p;
             if (T & 0x8000u)
               acc.add2((int)(T & 0xFFu), (int)((T >> 8) & 0x7Fu), S, W.x, W.y, Bv);
@@ -238,12 +251,13 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(TMEM ? RfCfg<K>::MAXREG_1C
       }
     }
     const int64_t cell = tile * 32 + lane;
-    double* qc = qout + cell * (int64_t)K * NQ + (int64_t)k1 * NQ + T.x;
+    const bool store = cell < ncells;
+    double* qc = qout + (store && rv.cells ? rv.cells[cell] : cell * (int64_t)K * NQ) + (int64_t)k1 * NQ + T.x;
     for (int m = 0; m < T.y; ++m) {
       const int q1 = T.x + m;
       const double v = acc.get(m, S);  // all lanes (tensor-memory loads are warp-wide)
       // conservation projection: (k1 = 0, q1 = 0..3) and (k1 = 1, q1 = 0) are zero
-      if (cell < ncells) qc[m] = ((k1 == 0 && q1 < 4) || (k1 == 1 && q1 == 0)) ? 0.0 : v;
+      if (store) qc[m] = ((k1 == 0 && q1 < 4) || (k1 == 1 && q1 == 0)) ? 0.0 : v;
     }
     __syncthreads();
   }
@@ -264,9 +278,12 @@ cudaError_t prepare_rf_k(size_t smem) {
 
 // Launches the persistent radial-first kernel (the queue was reset and the FP32 tiles
 // written by the caller).
+// ncells: the cells of a one-shape call, or (rv.count set) an upper bound of the shape's
+// cells in a ragged batch, which sizes the grid.
 template <int K, bool TMEM>
 cudaError_t launch_rf_k(const float* ftile32, int* queue, double* q, int64_t ncells, int NQ, const DevRadial& r,
-                        const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+                        const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                        const RaggedView& rv = RaggedView()) {
   constexpr int threads = 32 * K;
   const int64_t ntiles = (ncells + 31) / 32;
   const size_t smem = TMEM ? 0 : (size_t)r.n1max * threads * sizeof(double);
@@ -297,7 +314,7 @@ cudaError_t launch_rf_k(const float* ftile32, int* queue, double* q, int64_t nce
   if (group > ntiles) group = ntiles;
   rf_kernel<K, TMEM><<<(unsigned)grid, threads, smem, s>>>(ftile32, q, ncells, ntiles, NQ, r.tasks, r.chans, r.blocks,
                                                      r.uents, r.pw, r.order, r.ntasks, R32, queue, group,
-                                                     r.n1max, tcols);
+                                                     r.n1max, tcols, rv);
   if (ev1) cudaEventRecord(ev1, s);
   return cudaGetLastError();
 }

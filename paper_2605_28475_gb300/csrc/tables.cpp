@@ -397,8 +397,8 @@ std::string build_tables(int kmax, int lmax, Tables& t) {
               if (n1 > 127) return "a shell too large for the radial-first target encoding";
               const int32_t T = v[0].first | (v.size() > 1 ? v[1].first : 0) << 8 | (v.size() > 1 ? 1 << 15 : 0);
               RP.uents[u + 2 + j / 2] = (int32_t)((uint32_t)RP.uents[u + 2 + j / 2] | (uint32_t)T << (16 * (j & 1)));
-              RP.pw.push_back(v[0].second);
-              RP.pw.push_back(v.size() > 1 ? v[1].second : 0.0);
+              RP.pw.push_back(std::ldexp(v[0].second, kRfWeightExp));
+              RP.pw.push_back(v.size() > 1 ? std::ldexp(v[1].second, kRfWeightExp) : 0.0);
               cost += 2.0 * K * K + 2.0 * K * (double)v.size();
               RP.fp32_flops += 2.0 * K * K;
               RP.fp64_flops += 2.0 * K * (double)v.size();

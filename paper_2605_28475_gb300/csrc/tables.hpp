@@ -60,7 +60,11 @@ WEF_HD constexpr int rf_ctas_per_sm(int K) {
   return K <= 4 ? 8 : K == 5 ? 7 : K == 6 ? 6 : K == 7 ? 5 : K <= 9 ? 4 : 2;
 }
 WEF_HD constexpr int rf_group_width(int K, bool tmem) {
-  return tmem ? (K <= 9 ? 4 : 2) : (K <= 4 ? 4 : K <= 13 ? 2 : 1);
+#ifdef WEF_RF_J_OVERRIDE
+  return WEF_RF_J_OVERRIDE;
+#else
+  return tmem ? (K <= 9 ? 4 : 3) : (K <= 4 ? 4 : K <= 11 ? 2 : K <= 13 ? 3 : 1);
+#endif
 }
 
 // Radial-first program (paper Sec. 4.5.3 ordering with a dense two-stage radial
@@ -73,12 +77,14 @@ WEF_HD constexpr int rf_group_width(int K, bool tmem) {
 //   uents:  {q3 | mask << 16, pair_start, T_0 | T_1 << 16, T_2 | T_3 << 16}: each q3 paired
 //           with any q2 of the block, once; bit j of mask set if (q2_j, q3) is a pair, whose
 //           targets are T_j = (q1a - q1_base) | (q1b - q1_base) << 8 | (ne == 2) << 15 and
-//           whose weights pw[pair] = {ga, gb} (gb = 0 if ne = 1) follow from pair_start in
-//           j order
+//           whose weights pw[pair] = {ga, gb} * 2^kRfWeightExp (gb = 0 if ne = 1) follow from
+//           pair_start in j order (the kernel widens its FP32 products to FP64 scaled by
+//           2^-kRfWeightExp, see f2d_scaled in rf_kernel.cuh)
 // order:  task indices by decreasing cost (the persistent kernel's schedule).
 // Grouping by q2 makes stage 1 (2K^3 flops per q2 group) run over 4067 instead of 6125
 // groups at K = L = 12; walking the union of the block's q3 loads each f[:, q3] once per
 // block instead of once per pair (32707 instead of 56981 loads of K values for J = 2).
+constexpr int kRfWeightExp = 896;  // radial-first weights are stored as g * 2^896
 struct RadialProgram {
   std::vector<int32_t> tasks, chans, blocks, uents;
   std::vector<double> pw;

@@ -186,15 +186,16 @@ wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigne
         tc_pack_b_tile(K, true, Rt.data(), &Bt[(size_t)s * nt]);
       }
     }
-    // FP32 copy for the radial-first path, layout [sc][k1][k3][k2 -> KP4]: k2, the index the
-    // first radial stage contracts, fastest and padded with zeros to whole float4s.
-    const int KP4 = rf_k2_padded(K);
+    // FP32 copy for the radial-first path, layout [sc][k1][k2][k3 -> KP4]: rows over k3 (the
+    // index the first radial stage produces, two per packed FMA) padded with zeros to whole
+    // float4s.
+    const int KP4 = rf_row_padded(K);
     std::vector<float> R32((size_t)NS * K * K * KP4, 0.0f);
     for (int s = 0; s < NS; ++s)
       for (int k1 = 0; k1 < K; ++k1)
         for (int k2 = 0; k2 < K; ++k2)
           for (int k3 = 0; k3 < K; ++k3)
-            R32[(((size_t)s * K + k1) * K + k3) * KP4 + k2] = (float)R64[(((size_t)s * K + k3) * K + k1) * K + k2];
+            R32[(((size_t)s * K + k1) * K + k2) * KP4 + k3] = (float)R64[(((size_t)s * K + k3) * K + k1) * K + k2];
     op->release_core();
     cudaError_t e = upload(&op->d_R64, R64);
     if (e == cudaSuccess) e = upload(&op->d_R32, R32);

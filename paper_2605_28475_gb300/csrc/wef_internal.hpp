@@ -42,6 +42,18 @@ struct DevRadial {
   int n1max = 1;
 };
 
+// Where the cells of one shape of a ragged batch (wef_evaluate_ragged) are, as the
+// evaluation kernels see it: all three pointers are device data written by the batch's
+// set-up kernels on the stream, so nothing about the batch's composition is known on the
+// host.  All null (the default): the cells are [0, ncells) of a one-shape call, contiguous
+// in f and Q, with ncells known on the host.
+struct RaggedView {
+  const int* count = nullptr;          // cells of this shape
+  const int64_t* tile_off = nullptr;   // start of this shape's re-tiled f, in elements of the tile buffer
+  const int64_t* cells = nullptr;      // the batch's cell lists: offset (doubles) of a cell's values in f and Q
+  const int64_t* cells_off = nullptr;  // start of this shape's list (count entries) in `cells`
+};
+
 // Opts a kernel in to `bytes` of dynamic shared memory on the current device, once per
 // device and size (function attributes are per device).  `done` holds one entry per device.
 constexpr int kMaxDevices = 64;
@@ -64,8 +76,8 @@ cudaError_t smem_opt_in(Fn fn, size_t bytes, std::atomic<size_t>* done) {
 // Releases the cuBLAS handle of the dense baseline.
 void destroy_cublas(void* handle);
 
-// Radial-first FP32 core layout [sc][k1][k3][k2 -> KP4]: k2 padded to whole float4s.
-inline int rf_k2_padded(int K) { return (K + 3) / 4 * 4; }
+// Radial-first FP32 core layout [sc][k1][k2][k3 -> KP4]: rows over k3 padded to whole float4s.
+inline int rf_row_padded(int K) { return (K + 3) / 4 * 4; }
 
 // Radial-first kernel attributes for operators of radial size K and largest shell n1max,
 // set ahead of launches that may be captured in a graph.
@@ -78,13 +90,20 @@ cudaError_t launch_rf(int K, const double* f, float* ftile32, int* queue, double
                       const DevRadial& r, const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                       cudaEvent_t ev1 = nullptr);
 
+// The persistent radial-first kernel alone over one shape of a ragged batch: ftile32 is the
+// base of the batch's FP32 tiles (the shape's start is *rv.tile_off), queue this shape's
+// zeroed queue word, ncells_bound an upper bound of *rv.count (sizes the grid).
+cudaError_t launch_rf_ragged(int K, const float* ftile32, int* queue, double* q, int64_t ncells_bound, int NQ,
+                             const DevRadial& r, const float* R32, int nsm, const RaggedView& rv, cudaStream_t s);
+
 // f[ncells][K][NQ] -> ftile[tile][q][k][32] (zero-padded tail cells).
 cudaError_t launch_tile_f(const double* f, double* ftile, int64_t ncells, int K, int NQ, cudaStream_t s);
 
 // FP64 angular coupling + FP64 radial contraction + conservation projection.
 // chunks: device array of nchunks+1 task bounds.
 cudaError_t launch_fp64(int K, const double* ftile, double* q, int64_t ncells, int NQ, const DevProgram& p,
-                        const int32_t* chunks, int nchunks, const double* R64, cudaStream_t s);
+                        const int32_t* chunks, int nchunks, const double* R64, cudaStream_t s,
+                        const RaggedView& rv = RaggedView());
 
 // Tensor-core path: bytes of one packed core tile (MMA B operand) and its packing.
 int tc_b_tile_bytes(int K, bool tf32);

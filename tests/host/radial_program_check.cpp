@@ -70,8 +70,8 @@ int main() {
               if (ne < 1 || ne > 2 || a < 0 || a >= n1 || b < 0 || b >= n1) { bad++; printf("pair bad\n"); }
               for (int k1 = 0; k1 < K; ++k1) {
                 double Bv = 0; for (int k3 = 0; k3 < K; ++k3) Bv += A[j][k1 * K + k3] * f[k3 * NQ + q3];
-                Q[k1 * NQ + q1b + a] += P.pw[2*p] * Bv;
-                if (ne > 1) Q[k1 * NQ + q1b + b] += P.pw[2*p+1] * Bv;
+                Q[k1 * NQ + q1b + a] += std::ldexp(P.pw[2*p], -kRfWeightExp) * Bv;
+                if (ne > 1) Q[k1 * NQ + q1b + b] += std::ldexp(P.pw[2*p+1], -kRfWeightExp) * Bv;
               }
               ++p; ++npairs_seen;
             }

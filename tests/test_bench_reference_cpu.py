@@ -47,3 +47,20 @@ def test_clock_summary_parsing():
     assert d["reasons"] == ["hw_slowdown", "sw_power_cap"]
     s.lines = []
     assert s.summary()["reasons"] == ["unsampled"]
+
+
+def test_error_vs_oracle_guard():
+    """The bench line's per-cell error: the infinity norm of each cell's error over its rows,
+    relative to max(|Q_oracle| of the cell, 2^-10 x its largest sum of |terms|)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+
+    Qo = np.array([[1.0, -2.0], [1e-9, 0.0]])
+    T = np.array([[3.0, 4.0], [1.0, 1.0]])
+    Q = Qo + np.array([[1e-6, 0.0], [0.0, 1e-9]])
+    e = bench.error_vs_oracle(Q, Qo, T)
+    assert abs(e["max"] - 1e-9 / 2.0 ** -10) < 1e-18  # cell 2: guarded by its terms, not by |Q| = 1e-9
+    assert abs(e["median"] - (5e-7 + 1e-9 * 2.0 ** 10) / 2) < 1e-15
+    assert abs(e["plain_rel_max"] - 1.0) < 1e-12

@@ -1,5 +1,6 @@
-"""Continuous batching: every request's result is the same alone and in the mix; memory
-admission defers and rejects as it should."""
+"""Continuous batching: every request's result, delivered to host memory, is the same alone
+and in the mix (batches of one shape on the tensor-core paths, ragged batches mixing shapes
+on the radial-first and FP64 paths); memory admission defers and rejects as it should."""
 import numpy as np
 import pytest
 
@@ -44,10 +45,12 @@ def test_alone_equals_in_mix(prec):
     res = serve.run(srv, reqs)
     assert res["completed"] == len(reqs) and res["rejected"] == 0
     assert res["batches"] < len(reqs)  # requests were batched together
+    if prec in ("rf32", "fp64"):  # one ragged batch mixes shapes
+        assert srv.ragged
     for r in srv.completed:
         alone = ops[r.shape].evaluate(torch.from_numpy(r.f).cuda(), precision=prec)
         torch.cuda.synchronize()
-        assert torch.equal(r.q, alone), r.rid
+        assert torch.equal(r.q, alone.cpu()), r.rid
 
 
 def test_rejects_what_never_fits():
@@ -58,3 +61,25 @@ def test_rejects_what_never_fits():
     small = serve.Request(0.0, 1, (4, 4), wi.random_cells(4, 4, 10, seed=3))
     res = serve.run(srv, [big, small])
     assert res["rejected"] == 1 and res["completed"] == 1 and srv.completed[0].rid == 1
+
+
+def test_pinned_requests_mixed_shapes():
+    """Requests set up with pin_requests (pinned inputs and outputs, no page-locking while
+    serving), four shapes mixed in every batch: results equal the requests evaluated alone."""
+    shapes = [(4, 4), (6, 6), (8, 8), (12, 12)]
+    ops = {}
+    for i, (km, lm) in enumerate(shapes):
+        op = W.Operator(km, lm, 1.0)
+        op.upload_core(wi.random_core(len(gaunt.channels(lm)), km, seed=60 + i))
+        ops[(km, lm)] = op
+    reqs = [serve.Request(0.001 * i, i, shapes[i % 4], wi.random_cells(*shapes[i % 4], 1 + (37 * i) % 90, seed=700 + i))
+            for i in range(24)]
+    raw = [r.f.copy() for r in reqs]
+    serve.pin_requests(reqs)
+    srv = serve.Server(ops, arena_bytes=256 << 20, nslots=4, precision="rf32", max_batch_cells=400)
+    res = serve.run(srv, reqs)
+    assert res["completed"] == len(reqs) and res["batches"] < len(reqs)
+    for r in srv.completed:
+        alone = ops[r.shape].evaluate(torch.from_numpy(raw[r.rid]).cuda(), precision="rf32")
+        torch.cuda.synchronize()
+        assert torch.equal(r.out, alone.cpu()), r.rid

@@ -49,6 +49,9 @@ def test_pack_batch_caps():
     # the oldest request goes alone even if it exceeds both caps
     assert [r.f.shape[0] for r in serve.pack_batch([mk(5000)] + w, 450, cost, 0.35)] == [5000]
     assert serve.pack_batch([], 450) == []
+    # mixed batches (ragged evaluation): every shape, still in arrival order and within the caps
+    assert [r.f.shape[0] for r in serve.pack_batch(w, 450, mixed=True)] == [100, 50, 300]
+    assert [r.f.shape[0] for r in serve.pack_batch(w, 10_000, cost, 0.5, mixed=True)] == [100, 50]
 
 
 class _FakeServer:
@@ -85,6 +88,10 @@ class _FakeServer:
         self.in_flight = []
         return n
 
+    def wait(self, timeout):
+        if timeout:
+            __import__("time").sleep(min(timeout, 1e-3))
+
     def idle(self):
         return not self.in_flight
 
@@ -103,3 +110,15 @@ def test_run_loop_accounts_for_every_request():
     assert out["cells"] == sum(r.f.shape[0] for r in srv.completed)
     assert out["p50_ms"] is not None and out["p50_ms"] <= out["p99_ms"]
     assert out["batches"] == srv.batches <= out["completed"]
+
+
+def test_pin_requests():
+    """Set-up of a request stream: every request's cells copied into one pinned buffer, each
+    with a pinned output of the same shape."""
+    if not torch.cuda.is_available():
+        pytest.skip("pinned host memory needs a CUDA driver")
+    reqs = [serve.Request(0.0, i, (1, 1), np.full((i + 1, 2, 4), float(i))) for i in range(3)]
+    fin, fout = serve.pin_requests(reqs)
+    assert fin.is_pinned() and fout.is_pinned() and fin.numel() == 2 * 4 * 6
+    for i, r in enumerate(reqs):
+        assert tuple(r.f.shape) == (i + 1, 2, 4) and bool((r.f == float(i)).all()) and r.out.shape == r.f.shape

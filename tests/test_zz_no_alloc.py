@@ -4,7 +4,9 @@ cudaMalloc's implicit synchronisation is not allowed).  It uses a fixed scratch 
 by the library instead of a caller workspace.
 
 Checked through the C ABI against wef_evaluate on two calls in a row (the scratch keeps the
-previous call's contents), plus the size limit.  This file is collected last on purpose."""
+previous call's contents), on a batch smaller than one 32-cell tile and at the size limit
+(928 cells at Kmax = Lmax = 12 accepted, 929 rejected); after a first call, further calls
+leave the device's free memory unchanged.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -33,7 +35,7 @@ def _rel(a, b):
     return float((a - b).abs().max() / max(float(b.abs().max()), 1e-300))
 
 
-@pytest.mark.parametrize("km,lm,ncells", [(4, 4, 77), (12, 12, 600)])
+@pytest.mark.parametrize("km,lm,ncells", [(4, 4, 77), (4, 4, 5), (12, 12, 600), (12, 12, 928)])
 def test_noalloc_matches_evaluate_twice(km, lm, ncells):
     op = W.Operator(km, lm, 1.0)
     op.upload_core(wi.random_core(len(gaunt.channels(lm)), km, seed=21))
@@ -53,9 +55,27 @@ def test_noalloc_rejects_too_many_cells():
     km = lm = 12
     op = W.Operator(km, lm, 1.0)
     op.upload_core(wi.random_core(len(gaunt.channels(lm)), km, seed=22))
-    f = torch.zeros(1000, km + 1, (lm + 1) ** 2, dtype=torch.float64, device="cuda")
+    for n in (929, 1000):
+        f = torch.zeros(n, km + 1, (lm + 1) ** 2, dtype=torch.float64, device="cuda")
+        q = torch.empty_like(f)
+        with pytest.raises(W.WefError) as e:
+            W.wef_evaluate_noalloc(op.h, f.data_ptr(), q.data_ptr(), n, torch.cuda.current_stream().cuda_stream)
+        assert e.value.status == W.WEF_EINVAL and "928" in str(e.value)
+    op.close()
+
+
+def test_noalloc_allocates_nothing_after_first_call():
+    km = lm = 8
+    op = W.Operator(km, lm, 1.0)
+    op.upload_core(wi.random_core(len(gaunt.channels(lm)), km, seed=23))
+    f = torch.from_numpy(wi.random_cells(km, lm, 300, seed=24)).cuda()
     q = torch.empty_like(f)
-    with pytest.raises(W.WefError) as e:
-        W.wef_evaluate_noalloc(op.h, f.data_ptr(), q.data_ptr(), 1000, torch.cuda.current_stream().cuda_stream)
-    assert e.value.status == W.WEF_EINVAL and "928" in str(e.value)
+    st = torch.cuda.current_stream().cuda_stream
+    W.wef_evaluate_noalloc(op.h, f.data_ptr(), q.data_ptr(), 300, st)  # set-up call
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        W.wef_evaluate_noalloc(op.h, f.data_ptr(), q.data_ptr(), 300, st)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     op.close()
