@@ -763,7 +763,11 @@ def main():
     # configuration 5 (serving), timed after the headline legs
     serving = None
     if world == 1 and os.environ.get("WEF_BENCH_NO_SERVE") != "1" and args.duration > 0:
-        serving = serving_leg(args, W, torch, dev, args.duration)
+        try:  # the serving figure must not cost the benchmark line
+            serving = serving_leg(args, W, torch, dev, args.duration)
+        except Exception as e:  # noqa: BLE001
+            torch.cuda.synchronize(dev)
+            serving = {"error": f"{type(e).__name__}: {e}"}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -827,7 +831,8 @@ def main():
     if serving is not None:
         line["serving"] = {k: serving[k] for k in ("p50_ms", "p99_ms", "cells_per_s", "completed", "rejected",
                                                     "requests", "batches", "slowdown_p50", "slowdown_p99",
-                                                    "mean_queue_ms", "wall_s", "clocks", "note") if k in serving}
+                                                    "mean_queue_ms", "wall_s", "clocks", "note", "error")
+                           if k in serving}
     if world == 1 and os.environ.get("WEF_BENCH_NO_CPU") != "1":
         cb, (Qo, T, rows) = cpu_baseline(nsample, args.cpu_sample_rows, with_angular_first=True, R=R, f=f_host)
         line["cpu_baseline"] = cb

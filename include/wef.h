@@ -193,8 +193,9 @@ wef_status wef_plan_destroy(wef_plan plan);
  * 32-cell tiles, set up by kernels on `stream`), then each operator's contraction runs over
  * its own tiles on one of a few streams forked from `stream` and joined back to it.  Each
  * cell's result is bitwise the one wef_evaluate gives for that cell at the same precision.
- * The forked streams are created by the first call on each device (make that call before
- * any stream capture); calls from several host threads take turns queueing their work.
+ * The forked streams belong to the caller's stream and are created by the first call with
+ * that stream on a device (make that call before any stream capture); calls on different
+ * streams overlap; calls from several host threads take turns queueing their work.
  * Errors (checked before anything is queued): WEF_EINVAL (NULL argument, nops out of range,
  * a precision other than the two above, ncells < 0 or too large, workspace unaligned or too
  * small, an operator on another device), WEF_ENOCORE; WEF_ECUDA if a launch fails.

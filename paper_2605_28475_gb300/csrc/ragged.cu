@@ -6,11 +6,14 @@
 // operator and re-tile every operator's cells into its own 32-cell tiles; then each
 // operator's contraction kernel runs over its tiles, reading its cell count from the device
 // and writing each cell's Q at that cell's own offset.  The operators' contractions run on a
-// small pool of forked streams (created once per device) joined back to the caller's stream.
+// small pool of streams forked from the caller's stream (one pool per caller stream and
+// device, created at first use) and joined back to it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -112,17 +115,20 @@ __global__ void ragged_tile(Shapes sh, const double* __restrict__ f, const int* 
   }
 }
 
-// Forked streams for the operators' contractions, one pool per device, created by the
-// first call on that device; a lock keeps concurrent host threads from interleaving their
-// uses of the pool's events.
+// Forked streams for the operators' contractions: one pool per (device, caller stream), so
+// that calls on different caller streams (a server's slots) overlap instead of queueing on
+// shared forks; created by the first call with that stream on that device and kept until
+// the process exits.  A lock keeps concurrent host threads from interleaving their uses of
+// a pool's events.
 struct ForkPool {
   bool ready = false;
   cudaStream_t fork[kForks] = {};
   cudaEvent_t ev[kForks + 1] = {};
 };
 constexpr int kMaxDev = 64;
+constexpr size_t kMaxPools = 256;
 std::mutex g_pool_mutex;
-ForkPool g_pool[kMaxDev];
+std::map<std::pair<int, cudaStream_t>, ForkPool> g_pools;
 
 cudaError_t pool_setup(ForkPool& P) {
   if (P.ready) return cudaSuccess;
@@ -131,6 +137,14 @@ cudaError_t pool_setup(ForkPool& P) {
   for (int i = 0; i <= kForks && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&P.ev[i], cudaEventDisableTiming);
   if (e == cudaSuccess) P.ready = true;
   return e;
+}
+
+// The pool of (dev, s); beyond kMaxPools caller streams, calls share the pool of the
+// device's default stream.
+ForkPool& pool_for(int dev, cudaStream_t s) {
+  auto key = std::make_pair(dev, s);
+  if (g_pools.size() >= kMaxPools && !g_pools.count(key)) key = std::make_pair(dev, (cudaStream_t) nullptr);
+  return g_pools[key];
 }
 
 wef_status check_ops(const char* fn, const wef_op* ops, int nops, wef_precision prec, int* dev_out) {
@@ -243,7 +257,7 @@ wef_status wef_evaluate_ragged(const wef_op* ops, int nops, const int32_t* shape
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
     std::lock_guard<std::mutex> lock(g_pool_mutex);
-    ForkPool& P = g_pool[dev];
+    ForkPool& P = pool_for(dev, s);
     e = pool_setup(P);
     if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("wef_evaluate_ragged: streams: ") + cudaGetErrorString(e));
     const int nf = std::min(kForks, nops);

@@ -29,13 +29,14 @@ __device__ __forceinline__ double f2d_scaled(float x) {
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
-// c + a * b on a pair of FP32 values (two independent FMAs, each rounded once).
+// c + a * b on a pair of FP32 values (two independent FMAs, each rounded once): one packed
+// FP32x2 instruction, or two scalar ones (same results).
+template <bool PACKED>
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-#ifdef WEF_RF_SCALAR_FMA
-  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
-#else
-  return __ffma2_rn(a, b, c);
-#endif
+  if constexpr (PACKED)
+    return __ffma2_rn(a, b, c);
+  else
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
 }
 
 // The shell's FP64 accumulators Q[k1 = warp][q1 offset m][cell = lane], in shared memory
@@ -46,9 +47,11 @@ struct AccSmem {
     for (int m = 0; m < n1; ++m) p[m * S] = 0.0;
   }
   __device__ __forceinline__ void add(int m, int S, double w, double b) const { p[m * S] = fma(w, b, p[m * S]); }
+  // the two targets of a pair are distinct q1: both loads are issued before either update
   __device__ __forceinline__ void add2(int ma, int mb, int S, double wa, double wb, double b) const {
-    p[ma * S] = fma(wa, b, p[ma * S]);
-    p[mb * S] = fma(wb, b, p[mb * S]);
+    const double a = p[ma * S], c = p[mb * S];
+    p[ma * S] = fma(wa, b, a);
+    p[mb * S] = fma(wb, b, c);
   }
   __device__ __forceinline__ double get(int m, int S) const { return p[m * S]; }
 };
@@ -104,6 +107,9 @@ template <int K>
 struct RfCfg {
   static constexpr int KH = (K + 1) / 2;      // k3 pairs
   static constexpr int KP4 = (K + 3) / 4 * 4;  // padded k3 (float4 core rows)
+  // packed FP32x2 FMAs up to K = 13; two scalar FMAs above, where the tensor-memory
+  // variant runs (measured at K = 17: 60.9k against 59.2k cells/s with packed ones)
+  static constexpr bool PACKED = K <= 13;
   static constexpr int J = rf_group_width(K, false);  // q2 groups per block, shared-memory variant
   // CTAs per SM the register budget is sized for: about 32-36 resident warps where the
   // accumulators of a Kmax = Lmax shell let that many CTAs share the shared memory.  Each of
@@ -211,8 +217,8 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(TMEM ? RfCfg<K>::MAXREG_1C
             const float4 r = __ldg(Ra + k2 * R4 + c);
 #pragma unroll
             for (int j = 0; j < J; ++j) {
-              if (2 * c < KH) A2[j][2 * c] = fma2(make_float2(r.x, r.y), fd[j], A2[j][2 * c]);
-              if (2 * c + 1 < KH) A2[j][2 * c + 1] = fma2(make_float2(r.z, r.w), fd[j], A2[j][2 * c + 1]);
+              if (2 * c < KH) A2[j][2 * c] = fma2<Cfg::PACKED>(make_float2(r.x, r.y), fd[j], A2[j][2 * c]);
+              if (2 * c + 1 < KH) A2[j][2 * c + 1] = fma2<Cfg::PACKED>(make_float2(r.z, r.w), fd[j], A2[j][2 * c + 1]);
             }
           }
         }
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(TMEM ? RfCfg<K>::MAXREG_1C
             if (!((mask >> j) & 1)) continue;
             float2 b = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int i = 0; i < KH; ++i) b = fma2(A2[j][i], xp[i], b);
+            for (int i = 0; i < KH; ++i) b = fma2<Cfg::PACKED>(A2[j][i], xp[i], b);
             const double Bv = f2d_scaled(b.x + b.y);
             const uint32_t T = ((uint32_t)(j < 2 ? U.z : U.w) >> (16 * (j & 1))) & 0xFFFFu;  // targets
             const double2 W = __ldg(pw + p);  // Gaunt weights x 2^896

@@ -51,8 +51,11 @@ struct Program {
 WEF_HD constexpr bool rf_uses_tmem(int K, int n1max) {
   return 2 * ((long long)n1max * 32 * K * 8 + 1024) > 228LL * 1024;
 }
-// q2 groups the radial-first kernel keeps in registers at once: its register budget is
-// that of two CTAs per SM with shared-memory accumulators, of one with tensor memory.
+// q2 groups the radial-first kernel keeps in registers at once (rf_group_width): its
+// register budget is that of two CTAs per SM with shared-memory accumulators, of one with
+// tensor memory.  Three groups at K = 12-13 (measured at K = 13 with the next union record
+// prefetched: 379.7k against 343.2k cells/s with two) and with tensor memory above K = 9
+// (K = 17: 56.9k against 49.1k); four overflow the registers there.
 // CTAs per SM the shared-memory variant's register budget is sized for: about 32-36
 // warps for K <= 9 (measured at K = 9: 3.63M cells/s with 4 CTAs of 56 registers against
 // 2.81M with 2 of 96); two from K = 10 on, where the tighter budget spills (-2 to -5%).
@@ -60,11 +63,7 @@ WEF_HD constexpr int rf_ctas_per_sm(int K) {
   return K <= 4 ? 8 : K == 5 ? 7 : K == 6 ? 6 : K == 7 ? 5 : K <= 9 ? 4 : 2;
 }
 WEF_HD constexpr int rf_group_width(int K, bool tmem) {
-#ifdef WEF_RF_J_OVERRIDE
-  return WEF_RF_J_OVERRIDE;
-#else
   return tmem ? (K <= 9 ? 4 : 3) : (K <= 4 ? 4 : K <= 11 ? 2 : K <= 13 ? 3 : 1);
-#endif
 }
 
 // Radial-first program (paper Sec. 4.5.3 ordering with a dense two-stage radial

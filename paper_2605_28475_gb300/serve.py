@@ -168,6 +168,7 @@ class Server:
         self.completed = []
         self.rejected = []
         self.batches = 0
+        self.batch_log = []  # the requests of every launched batch
         self._done = queue.Queue()
         self._ready = []
 
@@ -196,14 +197,15 @@ class Server:
         return allocs
 
     def _tags(self, slot, chosen, cells):
-        """Pinned host arrays (operator index int32, then offset int64 per cell) of a batch."""
+        """Pinned host arrays of a batch: the offset (int64) of every cell, then its operator
+        index (int32), so that both device arrays are naturally aligned."""
         torch = self.torch
         st = self.staging[slot]
         if st is None or st.numel() < cells * 12:
             st = self.staging[slot] = torch.empty(max(cells, self.max_batch_cells, 4096) * 12,
                                                   dtype=torch.uint8).pin_memory()
-        ids = st[:cells * 4].view(torch.int32).numpy()
-        offs = st[cells * 4:cells * 12].view(torch.int64).numpy()
+        offs = st[:cells * 8].view(torch.int64).numpy()
+        ids = st[cells * 8:cells * 12].view(torch.int32).numpy()
         c = v = 0
         for r in chosen:
             n, N = r.f.shape[0], _n_per_cell(r.shape)
@@ -246,7 +248,7 @@ class Server:
                     to = allocs[2][0]
                     self.arena.view(to, cells * 12, torch.uint8).copy_(self._tags(slot, chosen, cells),
                                                                        non_blocking=True)
-                    wef_evaluate_ragged(self.handles, self.arena.ptr(to), self.arena.ptr(to + 4 * cells),
+                    wef_evaluate_ragged(self.handles, self.arena.ptr(to + 8 * cells), self.arena.ptr(to),
                                         self.arena.ptr(fo), self.arena.ptr(qo), cells, self.prec,
                                         self.arena.ptr(wo), wn, st.cuda_stream)
                 else:
@@ -273,6 +275,7 @@ class Server:
             ev.record(st)
         self.slot_busy[slot] = (chosen, allocs)
         self.batches += 1
+        self.batch_log.append(list(chosen))
         threading.Thread(target=self._waiter, args=(slot, ev), daemon=True).start()
         return True
 

@@ -72,13 +72,15 @@ def test_pinned_requests_mixed_shapes():
         op = W.Operator(km, lm, 1.0)
         op.upload_core(wi.random_core(len(gaunt.channels(lm)), km, seed=60 + i))
         ops[(km, lm)] = op
-    reqs = [serve.Request(0.001 * i, i, shapes[i % 4], wi.random_cells(*shapes[i % 4], 1 + (37 * i) % 90, seed=700 + i))
+    # a burst: everything arrives together, so batches must mix shapes
+    reqs = [serve.Request(0.0, i, shapes[i % 4], wi.random_cells(*shapes[i % 4], 1 + (37 * i) % 90, seed=700 + i))
             for i in range(24)]
     raw = [r.f.copy() for r in reqs]
     serve.pin_requests(reqs)
     srv = serve.Server(ops, arena_bytes=256 << 20, nslots=4, precision="rf32", max_batch_cells=400)
     res = serve.run(srv, reqs)
     assert res["completed"] == len(reqs) and res["batches"] < len(reqs)
+    assert any(len({r.shape for r in b}) > 1 for b in srv.batch_log)  # a batch mixed shapes
     for r in srv.completed:
         alone = ops[r.shape].evaluate(torch.from_numpy(raw[r.rid]).cuda(), precision="rf32")
         torch.cuda.synchronize()
