@@ -549,6 +549,20 @@ def bench_ragged(args, W, torch, dev, world, ncells=32768, seed=4):
     rstep = lambda: W.wef_plan_graph_launch(rplan, f.data_ptr(), q.data_ptr(), rws.data_ptr(), rws.numel(), st.cuda_stream)  # noqa: E731
     rms = _time_steps(rstep, args.steps, args.warmup, st, torch)
     W.wef_plan_destroy(rplan)
+    # the same batch through wef_evaluate_ragged: each cell's operator and offset as device
+    # arrays, the batch's composition worked out on the device (no plan), cells shuffled
+    perm = torch.from_numpy(np.random.default_rng(seed).permutation(ncells)).to(dev)
+    sizes = [(km + 1) * (lm + 1) ** 2 for km, lm in shapes]
+    sid = torch.from_numpy(np.repeat(np.arange(len(shapes), dtype=np.int32), counts)).to(dev)
+    starts = np.concatenate([[0], np.cumsum([n * sz for n, sz in zip(counts, sizes)])[:-1]])
+    off = torch.from_numpy(np.concatenate([st0 + sz * np.arange(n, dtype=np.int64)
+                                           for st0, sz, n in zip(starts, sizes, counts)])).to(dev)
+    sid, off = sid[perm].contiguous(), off[perm].contiguous()
+    hs = [o.h for o in ops]
+    gws = torch.empty(W.wef_ragged_workspace_size(hs, ncells, W.WEF_RADIAL_FP32), dtype=torch.uint8, device=dev)
+    gstep = lambda: W.wef_evaluate_ragged(hs, sid.data_ptr(), off.data_ptr(), f.data_ptr(), q.data_ptr(), ncells,  # noqa: E731
+                                          W.WEF_RADIAL_FP32, gws.data_ptr(), gws.numel(), st.cuda_stream)
+    gms = _time_steps(gstep, args.steps, args.warmup, st, torch)
     return _line("Q(f,f) cell-evals/s, ragged (Kmax,Lmax) in {6..16}^2", ncells / (ms / 1e3), "cells/s", ms, args, world,
                  "f64+tf32",
                  f"VHS gamma=0.5, {ncells} cells, (Kmax, Lmax) drawn independently per cell, 25 shapes grouped; one "
@@ -557,6 +571,10 @@ def bench_ragged(args, W, torch, dev, world, ncells=32768, seed=4):
                  roofline={"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": achieved / FP64_PEAK_TFLOPS, "fp64_flops_total": flops},
                  gpu_launches=2 * args.steps,
+                 ragged_call={"cells_per_s": ncells / (gms / 1e3), "ms_per_step": gms,
+                              "note": "same batch, cells shuffled, through wef_evaluate_ragged (per-cell operator and "
+                                      "offset on the device; set-up kernels, then each operator's persistent "
+                                      "radial-first launch on streams forked from the caller's)"},
                  radial_first={"cells_per_s": ncells / (rms / 1e3), "ms_per_step": rms, "fork_streams": rg,
                                "note": "same batch, radial-first plan: per-shape persistent launches on concurrent "
                                        "streams in one CUDA graph"})
