@@ -69,6 +69,10 @@ def parse():
                          "factorised vs naive-COO vs dense tensor at K=L=8; rk4: device RK4 and linearized "
                          "products at K=L=12; core: GPU vs host assembly of the core at K=L=12")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--serve-slots", type=int, default=8, help="serve: stream slots (batches in flight)")
+    ap.add_argument("--serve-batch-ms", type=float, default=50.0, help="serve: estimated GPU time cap per batch")
+    ap.add_argument("--variants", default="all", choices=["all", "none"],
+                    help="kl12: also time the other precisions (all) or only --precision (none)")
     return ap.parse_args()
 
 
@@ -623,18 +627,18 @@ def serving_leg(args, W, torch, dev, duration):
     cost = {sh: 1.0 / c for sh, c in cap.items()}
     # batches capped at ~50 ms of estimated GPU time so that small requests do not queue
     # behind one huge batch (a single larger request still goes alone)
-    srv = serve.Server(ops, arena_bytes=24 << 30, nslots=8, precision=args.precision, device=str(dev),
-                       cost_per_cell=cost, max_batch_s=0.05)
+    srv = serve.Server(ops, arena_bytes=24 << 30, nslots=args.serve_slots, precision=args.precision, device=str(dev),
+                       cost_per_cell=cost, max_batch_s=args.serve_batch_ms / 1e3)
     with ClockSampler(dev.index or 0) as clk:
-        res = serve.run(srv, reqs, service_s=lambda r: r.f.shape[0] * cost[r.shape])
+        res = serve.run(srv, reqs)
     res["clocks"] = clk.summary()
     res.update(rate_req_per_s=rate, duration_s=duration, ragged_batches=srv.ragged,
                capacity_cells_per_s={f"{k[0]}x{k[1]}": v for k, v in cap.items()},
                note=(f"Poisson arrivals at 0.7x capacity ({rate:.1f} req/s) for {duration:.0f} s; sizes log-uniform "
-                     f"1-{max_cells} cells; Kmax=Lmax in {{8,10,12,16}}; 8 stream slots; 24 GiB admission arena; "
-                     f"batches {'mixing every shape (wef_evaluate_ragged)' if srv.ragged else 'of one shape'}, capped "
-                     f"at 50 ms of estimated GPU time; latency = arrival to Q in pinned host memory; slowdown = "
-                     f"latency / the request's own service time at full-batch speed; cores "
+                     f"1-{max_cells} cells; Kmax=Lmax in {{8,10,12,16}}; {args.serve_slots} stream slots; 24 GiB admission "
+                     f"arena; batches {'mixing every shape (wef_evaluate_ragged)' if srv.ragged else 'of one shape'}, "
+                     f"capped at {args.serve_batch_ms:g} ms of estimated GPU time; latency = arrival to Q in pinned "
+                     f"host memory (small: requests of <= 64 cells, large: >= 1024 cells); cores "
                      + ("from the library quadrature" if real else "random stand-ins (timing does not depend on values)")))
     for op in ops.values():
         op.close()
@@ -743,7 +747,8 @@ def main():
         return out
 
     variants = {}
-    order = [p for p in ("fp64", "bf16", "tf32", "rf32") if p != args.precision] + [args.precision]
+    order = ([p for p in ("fp64", "bf16", "tf32", "rf32") if p != args.precision] if args.variants == "all" else []) \
+        + [args.precision]
     nsample = min(args.cpu_sample_cells, ncells)
     q_sample, invariant_max = {}, {}
     qv = q.view(ncells, KMAX + 1, (LMAX + 1) ** 2)
@@ -835,7 +840,7 @@ def main():
             "peak_probe": probe,
         },
         "variants": {k: {kk: vv for kk, vv in v.items() if kk not in ("step", "clocks")} for k, v in variants.items()},
-        "speedup_vs_fp64": head["value"] / variants["fp64"]["value"],
+        "speedup_vs_fp64": head["value"] / variants["fp64"]["value"] if "fp64" in variants else None,
         "e2e": {
             "value": world * ncells / (e2e_ms / 1e3),
             "unit": "cells/s",
@@ -848,8 +853,8 @@ def main():
     }
     if serving is not None:
         line["serving"] = {k: serving[k] for k in ("p50_ms", "p99_ms", "cells_per_s", "completed", "rejected",
-                                                    "requests", "batches", "slowdown_p50", "slowdown_p99",
-                                                    "mean_queue_ms", "wall_s", "clocks", "note", "error")
+                                                    "requests", "batches", "small", "large", "mean_queue_ms",
+                                                    "wall_s", "clocks", "note", "error")
                            if k in serving}
     if world == 1 and os.environ.get("WEF_BENCH_NO_CPU") != "1":
         cb, (Qo, T, rows) = cpu_baseline(nsample, args.cpu_sample_rows, with_angular_first=True, R=R, f=f_host)

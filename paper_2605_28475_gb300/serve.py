@@ -335,11 +335,18 @@ def poisson_requests(rate, duration, shapes, max_cells, seed, make_cells):
     return out
 
 
-def run(server, requests, time_limit=None, service_s=None):
+def _percentiles(lat_s):
+    lat = np.asarray(lat_s)
+    if not lat.size:
+        return {"requests": 0, "p50_ms": None, "p99_ms": None}
+    return {"requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+
+
+def run(server, requests, time_limit=None, small_cells=64, large_cells=1024):
     """Replay `requests` (arrival times in seconds from now) through `server`; returns a
-    summary with p50/p99 arrival-to-completion latency (result in host memory) and
-    throughput.  service_s(request), if given, is the request's estimated service time
-    alone on the GPU, for the slowdown percentiles (latency / service time)."""
+    summary with p50/p99 arrival-to-completion latency (result in host memory), the same for
+    small (<= small_cells) and large (>= large_cells) requests, and throughput."""
     pending = list(requests)
     heapq.heapify(pending)
     waiting = []  # arrived, not yet launched (FIFO)
@@ -379,8 +386,6 @@ def run(server, requests, time_limit=None, service_s=None):
         "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
         "mean_queue_ms": float(np.mean([r.admitted - r.arrival for r in server.completed]) * 1e3) if lat.size else None,
     }
-    if service_s is not None and lat.size:
-        sl = np.array([(r.done - r.arrival) / max(service_s(r), 1e-9) for r in server.completed])
-        out["slowdown_p50"] = float(np.percentile(sl, 50))
-        out["slowdown_p99"] = float(np.percentile(sl, 99))
+    out["small"] = _percentiles([r.done - r.arrival for r in server.completed if r.f.shape[0] <= small_cells])
+    out["large"] = _percentiles([r.done - r.arrival for r in server.completed if r.f.shape[0] >= large_cells])
     return out

@@ -110,6 +110,9 @@ def test_run_loop_accounts_for_every_request():
     assert out["cells"] == sum(r.f.shape[0] for r in srv.completed)
     assert out["p50_ms"] is not None and out["p50_ms"] <= out["p99_ms"]
     assert out["batches"] == srv.batches <= out["completed"]
+    # latency by request size: small (<= 64 cells) and large (>= 1024 cells, none here)
+    assert out["small"]["requests"] == sum(1 for r in srv.completed if r.f.shape[0] <= 64)
+    assert out["large"]["requests"] == 0 and out["large"]["p50_ms"] is None
 
 
 def test_pin_requests():
