@@ -579,7 +579,8 @@ def bench_ragged(args, W, torch, dev, world, ncells=32768, seed=4):
                               "note": "same batch, cells shuffled, through wef_evaluate_ragged (per-cell operator and "
                                       "offset on the device; set-up kernels, then each operator's persistent "
                                       "radial-first launch on streams forked from the caller's)"},
-                 radial_first={"cells_per_s": ncells / (rms / 1e3), "ms_per_step": rms, "fork_streams": rg,
+                 radial_first={"cells_per_s": ncells / (rms / 1e3), "ms_per_step": rms, "fork_streams": rg % 16,
+                               "tile_group_mb": rg // 16 or 24,
                                "note": "same batch, radial-first plan: per-shape persistent launches on concurrent "
                                        "streams in one CUDA graph"})
 

@@ -140,7 +140,8 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
  * else about 8 items per SM).  Precision: WEF_MIXED_TF32 or WEF_MIXED_BF16.
  * With WEF_RADIAL_FP32 the plan runs the radial-first evaluation of each shape (one
  * persistent launch per shape, largest first) on `granularity` concurrent forked
- * streams (0 = cache, else 4), joined back to the caller's stream.
+ * streams (0 = cache, else 4), joined back to the caller's stream; its autotuned setting
+ * also fixes the launches' L2 tile-group size.
  * Every operator must have a core uploaded (Kmax >= 1 for the tensor-core path) and
  * must outlive the plan.
  * Set-up allocations happen in wef_plan_create only.
@@ -165,8 +166,10 @@ wef_status wef_plan_execute(wef_plan plan, const double* f_dev, double* q_dev, v
 wef_status wef_plan_graph_launch(wef_plan plan, const double* f_dev, double* q_dev, void* workspace,
                                  int64_t ws_bytes, void* stream);
 /* Autotuner: times the plan at granularities 1, 2, 4, ... (radial-first: 1, 2, 4, 8
- * streams) on the given buffers (synchronous), keeps the fastest, appends it to the
- * WEF_TUNE_CACHE file if set, and returns it in *chosen (may be NULL). */
+ * streams, each with L2 tile groups of 12, 24 and 48 MB of FP32 tiles - the group bounds
+ * what a group's tiles and Q rows occupy in L2) on the given buffers (synchronous), keeps
+ * the fastest, appends it to the WEF_TUNE_CACHE file if set, and returns it in *chosen
+ * (may be NULL; radial-first: streams + 16 * group MB). */
 wef_status wef_plan_autotune(wef_plan plan, const double* f_dev, double* q_dev, void* workspace, int64_t ws_bytes,
                              void* stream, int* chosen);
 /* Synchronous check of the plan's device status word (see wef_device_status). */

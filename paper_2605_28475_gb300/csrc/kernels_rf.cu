@@ -49,7 +49,7 @@ __global__ void tile_f32_kernel(const double* __restrict__ f, float* __restrict_
 // tensor-memory instantiations (kernels_rf_tmem.cu)
 cudaError_t launch_rf_tmem(int K, const float* ftile32, int* queue, double* q, int64_t ncells, int NQ,
                            const DevRadial& r, const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0,
-                           cudaEvent_t ev1, const RaggedView& rv);
+                           cudaEvent_t ev1, const RaggedView& rv, int64_t group_bytes);
 
 cudaError_t prepare_rf(int K, int n1max) {
   if (K < 1 || K > 17) return cudaErrorInvalidValue;
@@ -69,7 +69,7 @@ cudaError_t prepare_rf(int K, int n1max) {
 
 cudaError_t launch_rf(int K, const double* f, float* ftile32, int* queue, double* q, int64_t ncells, int NQ,
                       const DevRadial& r, const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0,
-                      cudaEvent_t ev1) {
+                      cudaEvent_t ev1, int64_t group_bytes) {
   if (K < 1 || K > 17) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
@@ -79,11 +79,11 @@ cudaError_t launch_rf(int K, const double* f, float* ftile32, int* queue, double
   // shared-memory accumulators while two CTAs of them fit in the 228 KB of an SM (the
   // program was built for the same choice: its q2 block width depends on it)
   if (rf_uses_tmem(K, r.n1max))
-    return launch_rf_tmem(K, ftile32, queue, q, ncells, NQ, r, R32, nsm, s, ev0, ev1, RaggedView());
+    return launch_rf_tmem(K, ftile32, queue, q, ncells, NQ, r, R32, nsm, s, ev0, ev1, RaggedView(), group_bytes);
   switch (K) {
 #define WEF_RF(k) \
   case k:         \
-    return rfk::launch_rf_k<k, false>(ftile32, queue, q, ncells, NQ, r, R32, nsm, s, ev0, ev1);
+    return rfk::launch_rf_k<k, false>(ftile32, queue, q, ncells, NQ, r, R32, nsm, s, ev0, ev1, RaggedView(), group_bytes);
     WEF_RF(1) WEF_RF(2) WEF_RF(3) WEF_RF(4) WEF_RF(5) WEF_RF(6) WEF_RF(7) WEF_RF(8) WEF_RF(9) WEF_RF(10) WEF_RF(11)
     WEF_RF(12) WEF_RF(13) WEF_RF(14) WEF_RF(15) WEF_RF(16) WEF_RF(17)
 #undef WEF_RF
@@ -96,7 +96,7 @@ cudaError_t launch_rf_ragged(int K, const float* ftile32, int* queue, double* q,
                              const DevRadial& r, const float* R32, int nsm, const RaggedView& rv, cudaStream_t s) {
   if (K < 1 || K > 17) return cudaErrorInvalidValue;
   if (rf_uses_tmem(K, r.n1max))
-    return launch_rf_tmem(K, ftile32, queue, q, ncells_bound, NQ, r, R32, nsm, s, nullptr, nullptr, rv);
+    return launch_rf_tmem(K, ftile32, queue, q, ncells_bound, NQ, r, R32, nsm, s, nullptr, nullptr, rv, 0);
   switch (K) {
 #define WEF_RF(k) \
   case k:         \

@@ -99,6 +99,7 @@ struct wef_plan_s {
   cudaStream_t fork[kMaxFork] = {};
   cudaEvent_t fork_ev[kMaxFork + 1] = {};
   int nfork = 4;
+  int group_mb = 0;  // L2 tile-group size of the shapes' launches, MB (0: the default)
 
   void release() {
     for (auto& s : fork)
@@ -208,8 +209,9 @@ wef_status plan_launch_rf(wef_plan_s* P, const double* f, double* q, void* ws, c
   for (int si : P->rf_order) {
     const RaggedShape& S = P->shapes[si];
     if (S.ncells == 0) continue;
-    st = wef_evaluate(P->ops[si], f + S.f_off, q + S.q_off, S.ncells, WEF_RADIAL_FP32,
-                      (char*)ws + P->rf_ws_off[si], P->rf_ws_len[si], P->fork[k % nf]);
+    st = evaluate_grouped(P->ops[si], f + S.f_off, q + S.q_off, S.ncells, WEF_RADIAL_FP32,
+                          (char*)ws + P->rf_ws_off[si], P->rf_ws_len[si], P->fork[k % nf],
+                          (int64_t)P->group_mb << 20);
     if (st != WEF_OK) break;
     ++k;
   }
@@ -338,9 +340,12 @@ wef_status wef_plan_create(const wef_op* ops, const int64_t* ncells, int nops, w
     if (e != cudaSuccess) return set_error(WEF_ECUDA, std::string("wef_plan_create: ") + cudaGetErrorString(e));
     if (rf) {
       // the tuned quantity is the number of concurrent shape streams
-      int nf = granularity > 0 ? granularity : cache_lookup(P->key);
+      // tuned value: streams + 16 * tile-group MB (an explicit granularity gives the streams)
+      const int v = granularity > 0 ? granularity : cache_lookup(P->key);
+      const int nf = v % 16;
       P->nfork = nf > 0 ? std::min(nf, (int)wef_plan_s::kMaxFork) : 4;
-      P->granularity = P->nfork;
+      P->group_mb = granularity > 0 ? 0 : v / 16;
+      P->granularity = P->nfork + 16 * P->group_mb;
       // kernel attributes of every shape now, outside any later stream capture
       for (size_t i = 0; i < P->ops.size() && e == cudaSuccess; ++i)
         e = prepare_rf(P->ops[i]->T.K, P->ops[i]->T.rprog.n1max);
@@ -436,9 +441,19 @@ wef_status wef_plan_autotune(wef_plan plan, const double* f_dev, double* q_dev, 
     int max_tasks = 1;
     for (wef_op op : plan->ops) max_tasks = std::max(max_tasks, op->T.prog4.ntasks());
     if (rf) max_tasks = wef_plan_s::kMaxFork;  // candidates: 1, 2, 4, 8 concurrent shape streams
+    // candidates: granularities 1, 2, 4, ...; radial-first: 1, 2, 4, 8 streams, each with L2
+    // tile groups of 12, 24 and 48 MB (encoded as streams + 16 * MB)
+    std::vector<int> cand;
     for (int g = 1; g <= 64 && g <= max_tasks; g *= 2) {
+      if (rf)
+        for (int mb : {12, 24, 48}) cand.push_back(g + 16 * mb);
+      else
+        cand.push_back(g);
+    }
+    for (int g : cand) {
       if (rf) {
-        plan->nfork = g;
+        plan->nfork = g % 16;
+        plan->group_mb = g / 16;
         plan->granularity = g;
         if (plan->gexec) {
           cudaGraphExecDestroy(plan->gexec);
@@ -468,7 +483,9 @@ wef_status wef_plan_autotune(wef_plan plan, const double* f_dev, double* q_dev, 
     cudaEventDestroy(e1);
     if (st != WEF_OK) return st;
     if (rf) {
-      plan->nfork = plan->granularity = best_g;
+      plan->nfork = best_g % 16;
+      plan->group_mb = best_g / 16;
+      plan->granularity = best_g;
       if (plan->gexec) {
         cudaGraphExecDestroy(plan->gexec);
         plan->gexec = nullptr;

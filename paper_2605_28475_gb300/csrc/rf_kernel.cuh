@@ -286,10 +286,11 @@ cudaError_t prepare_rf_k(size_t smem) {
 // written by the caller).
 // ncells: the cells of a one-shape call, or (rv.count set) an upper bound of the shape's
 // cells in a ragged batch, which sizes the grid.
+// group_bytes: FP32 tile bytes per L2 tile group (0: 24 MB).
 template <int K, bool TMEM>
 cudaError_t launch_rf_k(const float* ftile32, int* queue, double* q, int64_t ncells, int NQ, const DevRadial& r,
                         const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
-                        const RaggedView& rv = RaggedView()) {
+                        const RaggedView& rv = RaggedView(), int64_t group_bytes = 0) {
   constexpr int threads = 32 * K;
   const int64_t ntiles = (ncells + 31) / 32;
   const size_t smem = TMEM ? 0 : (size_t)r.n1max * threads * sizeof(double);
@@ -318,7 +319,7 @@ cudaError_t launch_rf_k(const float* ftile32, int* queue, double* q, int64_t nce
   // cells: 485 MB of DRAM traffic per launch against 729 MB with 48 MB groups (432 MB
   // algorithmic), 0.9% faster.
   const int64_t tile_bytes = (int64_t)NQ * K * 32 * sizeof(float);
-  int64_t group = (24LL << 20) / tile_bytes;
+  int64_t group = (group_bytes > 0 ? group_bytes : (24LL << 20)) / tile_bytes;
   if (group < 1) group = 1;
   if (group > ntiles) group = ntiles;
   rf_kernel<K, TMEM><<<(unsigned)grid, threads, smem, s>>>(ftile32, q, ncells, ntiles, NQ, r.tasks, r.chans, r.blocks,

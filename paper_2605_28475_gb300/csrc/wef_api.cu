@@ -226,6 +226,13 @@ wef_status wef_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int
 
 wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t ncells, wef_precision prec,
                         void* workspace, int64_t workspace_bytes, void* stream) {
+  return wef::evaluate_grouped(op, f_dev, q_dev, ncells, prec, workspace, workspace_bytes, stream, 0);
+}
+
+}  // extern "C"
+
+wef_status wef::evaluate_grouped(wef_op op, const double* f_dev, double* q_dev, int64_t ncells, wef_precision prec,
+                                 void* workspace, int64_t workspace_bytes, void* stream, int64_t group_bytes) {
   return wef::guarded("wef_evaluate", [&]() -> wef_status {
     if (!op) return fail(WEF_EINVAL, "wef_evaluate: op is NULL");
     if (!valid_precision(prec)) return fail(WEF_EINVAL, "wef_evaluate: unknown precision");
@@ -251,7 +258,7 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
                   (const int4*)op->r_uents, (const double2*)op->r_pw, op->r_order,
                   (int)RP.task_cost.size(), RP.n1max};
       cudaError_t er = launch_rf(K, f_dev, (float*)((char*)workspace + 256), (int*)workspace, q_dev, ncells, NQ, r,
-                                 op->d_R32, op->sms, s, op->trace_start, op->trace_stop);
+                                 op->d_R32, op->sms, s, op->trace_start, op->trace_stop, group_bytes);
       if (er != cudaSuccess) return cuda_fail(er, "wef_evaluate: radial-first kernels");
       return WEF_OK;
     }
@@ -278,6 +285,8 @@ wef_status wef_evaluate(wef_op op, const double* f_dev, double* q_dev, int64_t n
     return WEF_OK;
   });
 }
+
+extern "C" {
 
 wef_status wef_core_build(wef_op op, int pad_rad, int pad_ang, double* R_out, int64_t len) {
   return wef::guarded("wef_core_build", [&]() -> wef_status {

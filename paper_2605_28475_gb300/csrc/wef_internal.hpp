@@ -85,10 +85,16 @@ cudaError_t prepare_rf(int K, int n1max);
 
 // Radial-first evaluation: FP32 re-tiling of f, then the persistent radial-first
 // kernel (queue reset here).  ftile32 and queue live in the caller's workspace.
-// ev0/ev1 (may be null) are recorded around the contraction kernel alone.
+// ev0/ev1 (may be null) are recorded around the contraction kernel alone.  group_bytes: FP32
+// tile bytes per L2 tile group (0: the default, 24 MB).
 cudaError_t launch_rf(int K, const double* f, float* ftile32, int* queue, double* q, int64_t ncells, int NQ,
                       const DevRadial& r, const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
-                      cudaEvent_t ev1 = nullptr);
+                      cudaEvent_t ev1 = nullptr, int64_t group_bytes = 0);
+
+// wef_evaluate with an explicit L2 tile-group size for the radial-first path (group_bytes,
+// 0: the default; ignored by the other precisions): the same checks, errors and results.
+wef_status evaluate_grouped(wef_op op, const double* f_dev, double* q_dev, int64_t ncells, wef_precision prec,
+                            void* workspace, int64_t workspace_bytes, void* stream, int64_t group_bytes);
 
 // The persistent radial-first kernel alone over one shape of a ragged batch: ftile32 is the
 // base of the batch's FP32 tiles (the shape's start is *rv.tile_off), queue this shape's
