@@ -41,10 +41,12 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # 1987 MHz with full warps), x 152 SMs x 2 flops x 2070 MHz maximum clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel at the default workload
-# (K=L=12, 16384 cells), from a one-pass ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of the kernel as it is now; None until such a capture exists.
-TRAFFIC_BYTES = {"rf32": None}
-TRAFFIC_NOTE = "not captured for this kernel version"
+# (K=L=12, 16384 cells), from a one-pass ncu capture of the timed step's launch
+# (dram__bytes_read.sum 211.02 MB + dram__bytes_write.sum 275.72 MB; command and reading in
+# profiles/rf_kernel_13_traffic_kl12_16384cells.md).  Re-capture whenever the kernel changes.
+TRAFFIC_BYTES = {"rf32": 486.74e6}
+TRAFFIC_NOTE = ("captured with the kernel version of this file's commit (24 MB L2 tile groups, J = 3, packed "
+                "FP32x2 stages); 48 MB groups moved 728.7 MB")
 # arithmetic types of each path: FP64 reductions and projection, plus the radial products
 DTYPES = {"fp64": "f64", "bf16": "f64+bf16", "tf32": "f64+tf32", "rf32": "f64+f32"}
 
