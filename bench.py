@@ -71,8 +71,10 @@ def parse():
                          "factorised vs naive-COO vs dense tensor at K=L=8; rk4: device RK4 and linearized "
                          "products at K=L=12; core: GPU vs host assembly of the core at K=L=12")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
-    ap.add_argument("--serve-slots", type=int, default=8, help="serve: stream slots (batches in flight)")
-    ap.add_argument("--serve-batch-ms", type=float, default=50.0, help="serve: estimated GPU time cap per batch")
+    ap.add_argument("--serve-slots", type=int, default=16, help="serve: stream slots (batches in flight)")
+    ap.add_argument("--serve-batch-ms", type=float, default=20.0, help="serve: estimated GPU time cap per batch")
+    ap.add_argument("--serve-max-wait-ms", type=float, default=100.0,
+                    help="serve: size-aware admission bound (0: arrival order)")
     ap.add_argument("--variants", default="all", choices=["all", "none"],
                     help="kl12: also time the other precisions (all) or only --precision (none)")
     return ap.parse_args()
@@ -631,7 +633,8 @@ def serving_leg(args, W, torch, dev, duration):
     # batches capped at ~50 ms of estimated GPU time so that small requests do not queue
     # behind one huge batch (a single larger request still goes alone)
     srv = serve.Server(ops, arena_bytes=24 << 30, nslots=args.serve_slots, precision=args.precision, device=str(dev),
-                       cost_per_cell=cost, max_batch_s=args.serve_batch_ms / 1e3)
+                       cost_per_cell=cost, max_batch_s=args.serve_batch_ms / 1e3,
+                       max_wait_s=args.serve_max_wait_ms / 1e3 if args.serve_max_wait_ms > 0 else None)
     with ClockSampler(dev.index or 0) as clk:
         res = serve.run(srv, reqs)
     res["clocks"] = clk.summary()
@@ -640,7 +643,10 @@ def serving_leg(args, W, torch, dev, duration):
                note=(f"Poisson arrivals at 0.7x capacity ({rate:.1f} req/s) for {duration:.0f} s; sizes log-uniform "
                      f"1-{max_cells} cells; Kmax=Lmax in {{8,10,12,16}}; {args.serve_slots} stream slots; 24 GiB admission "
                      f"arena; batches {'mixing every shape (wef_evaluate_ragged)' if srv.ragged else 'of one shape'}, "
-                     f"capped at {args.serve_batch_ms:g} ms of estimated GPU time; latency = arrival to Q in pinned "
+                     f"capped at {args.serve_batch_ms:g} ms of estimated GPU time; "
+                     + (f"size-aware admission (waiting > {args.serve_max_wait_ms:g} ms first, then cheapest first); "
+                        if args.serve_max_wait_ms > 0 else "arrival order; ")
+                     + f"latency = arrival to Q in pinned "
                      f"host memory (small: requests of <= 64 cells, large: >= 1024 cells); cores "
                      + ("from the library quadrature" if real else "random stand-ins (timing does not depend on values)")))
     for op in ops.values():

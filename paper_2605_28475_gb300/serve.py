@@ -2,8 +2,9 @@
 
 Requests (a batch of cells of one (Kmax, Lmax) operator) arrive over time and wait in a
 FIFO.  Whenever one of the stream slots is free, the scheduler packs waiting requests, in
-arrival order, up to a cell cap, an estimated GPU time per batch and what the device arena
-can hold, into one batch.  On the radial-first and FP64 paths a batch mixes requests of
+arrival order (or, with size-aware admission, overdue ones first and then the cheapest),
+up to a cell cap, an estimated GPU time per batch and what the device arena can hold, into
+one batch.  On the radial-first and FP64 paths a batch mixes requests of
 every shape and runs as one wef_evaluate_ragged call (each cell tagged with its operator
 and its position in the batch); on the tensor-core paths a batch holds one shape and runs
 as one wef_evaluate call.  Per batch, on the slot's stream: the requests' coefficients are
@@ -96,19 +97,30 @@ def _n_per_cell(shape):
     return (km + 1) * (lm + 1) ** 2
 
 
-def pack_batch(waiting, max_cells, cost_per_cell=None, max_batch_s=None, mixed=False):
-    """Waiting requests in arrival order (of the oldest request's shape only, unless `mixed`)
+def _cost(r, cost_per_cell):
+    return 0.0 if cost_per_cell is None else cost_per_cell.get(r.shape, 0.0) * r.f.shape[0]
+
+
+def pack_batch(waiting, max_cells, cost_per_cell=None, max_batch_s=None, mixed=False, now=None, max_wait_s=None):
+    """Waiting requests in arrival order (of the first candidate's shape only, unless `mixed`)
     while the batch stays within `max_cells` cells and (if costs are given) `max_batch_s`
-    seconds of estimated GPU time.  The oldest request is always taken, whatever its size."""
+    seconds of estimated GPU time.  The first candidate is always taken, whatever its size.
+    With `max_wait_s` (size-aware admission): requests waiting longer than that come first,
+    in arrival order, then the others by increasing estimated GPU time."""
     if not waiting:
         return []
-    shape = waiting[0].shape
+    seq = waiting
+    if max_wait_s is not None and now is not None:
+        late = [r for r in waiting if now - r.arrival > max_wait_s]
+        fresh = sorted((r for r in waiting if now - r.arrival <= max_wait_s), key=lambda r: _cost(r, cost_per_cell))
+        seq = late + fresh
+    shape = seq[0].shape
     chosen, cells, est = [], 0, 0.0
-    for r in waiting:
+    for r in seq:
         if r.shape != shape and not mixed:
             continue
         n = r.f.shape[0]
-        c = 0.0 if cost_per_cell is None else cost_per_cell.get(r.shape, 0.0) * n
+        c = _cost(r, cost_per_cell)
         if chosen and (cells + n > max_cells or (max_batch_s is not None and est + c > max_batch_s)):
             break
         chosen.append(r)
@@ -146,7 +158,7 @@ class Server:
     radial-first and FP64 paths) packs requests of every shape into one batch."""
 
     def __init__(self, ops, arena_bytes, nslots=8, precision="rf32", device="cuda:0", max_batch_cells=16384,
-                 keep_results=False, cost_per_cell=None, max_batch_s=None, ragged=None):
+                 keep_results=False, cost_per_cell=None, max_batch_s=None, ragged=None, max_wait_s=None):
         import torch
 
         self.torch = torch
@@ -164,6 +176,7 @@ class Server:
         self.max_batch_cells = int(max_batch_cells)
         self.cost_per_cell = cost_per_cell  # {shape: estimated seconds per cell}
         self.max_batch_s = max_batch_s
+        self.max_wait_s = max_wait_s  # size-aware admission bound (None: arrival order)
         self.keep = keep_results  # results are always delivered to Request.out; kept for compatibility
         self.completed = []
         self.rejected = []
@@ -222,7 +235,8 @@ class Server:
         slot = next((i for i, b in enumerate(self.slot_busy) if b is None), None)
         if slot is None or not waiting:
             return False
-        chosen = pack_batch(waiting, self.max_batch_cells, self.cost_per_cell, self.max_batch_s, mixed=self.ragged)
+        chosen = pack_batch(waiting, self.max_batch_cells, self.cost_per_cell, self.max_batch_s, mixed=self.ragged,
+                            now=now, max_wait_s=self.max_wait_s)
         allocs = self._alloc(self._bytes(chosen))
         while allocs is None and len(chosen) > 1:  # shrink the batch to what memory allows
             chosen.pop()

@@ -49,6 +49,11 @@ def test_pack_batch_caps():
     # the oldest request goes alone even if it exceeds both caps
     assert [r.f.shape[0] for r in serve.pack_batch([mk(5000)] + w, 450, cost, 0.35)] == [5000]
     assert serve.pack_batch([], 450) == []
+    # size-aware admission: overdue requests (waiting > 0.5 s at now = 1 s) first, in arrival
+    # order, then the others by increasing estimated time
+    w2 = [mk(100, t=0.2), mk(50, (12, 12), 0.8), mk(300, t=0.9), mk(10, t=0.95), mk(200, t=0.3)]
+    got = serve.pack_batch(w2, 10_000, cost, 10.0, mixed=True, now=1.0, max_wait_s=0.5)
+    assert [r.f.shape[0] for r in got] == [100, 200, 10, 50, 300]
     # mixed batches (ragged evaluation): every shape, still in arrival order and within the caps
     assert [r.f.shape[0] for r in serve.pack_batch(w, 450, mixed=True)] == [100, 50, 300]
     assert [r.f.shape[0] for r in serve.pack_batch(w, 10_000, cost, 0.5, mixed=True)] == [100, 50]
