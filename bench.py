@@ -42,13 +42,14 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel at the default workload
 # (K=L=12, 16384 cells), from a one-pass ncu capture of the timed step's launch
-# (dram__bytes_read.sum 211.02 MB + dram__bytes_write.sum 275.72 MB; command and reading in
+# (dram__bytes_read.sum 215.83 MB + dram__bytes_write.sum 278.35 MB; command and reading in
 # profiles/rf_kernel_13_traffic_kl12_16384cells.md).  Re-capture whenever the kernel changes.
-TRAFFIC_BYTES = {"rf32": 486.74e6}
-TRAFFIC_NOTE = ("captured with the kernel version of this file's commit (24 MB L2 tile groups, J = 3, packed "
-                "FP32x2 stages); 48 MB groups moved 728.7 MB")
+TRAFFIC_BYTES = {"rf32": 494.18e6}
+TRAFFIC_NOTE = ("captured with the kernel version of this file's commit (FP64 accumulators in tensor memory, two "
+                "CTAs per SM, 24 MB L2 tile groups, J = 3, packed FP32x2 stages); shared-memory accumulators moved "
+                "486.7 MB, 48 MB tile groups 728.7 MB")
 # arithmetic types of each path: FP64 reductions and projection, plus the radial products
-DTYPES = {"fp64": "f64", "bf16": "f64+bf16", "tf32": "f64+tf32", "rf32": "f64+f32"}
+DTYPES = {"fp64": "f64", "bf16": "f64+bf16", "tf32": "f64+tf32", "rf32": "f64+f32", "rftc": "f64+f32+3xtf32"}
 
 
 def parse():
@@ -56,7 +57,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="rf32", choices=["fp64", "bf16", "tf32", "rf32"])
+    ap.add_argument("--precision", default="rf32", choices=["fp64", "bf16", "tf32", "rf32", "rftc"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ncells", type=int, default=NCELLS)
     ap.add_argument("--kl", type=int, default=KMAX, help="Kmax = Lmax of the main workload (default 12)")
@@ -756,8 +757,10 @@ def main():
         return out
 
     variants = {}
-    order = ([p for p in ("fp64", "bf16", "tf32", "rf32") if p != args.precision] if args.variants == "all" else []) \
-        + [args.precision]
+    # the tensor-core radial-first path (rftc) is compiled for Kmax = 8, 10 and 12
+    others = [p for p in ("fp64", "bf16", "tf32", "rftc", "rf32")
+              if p != args.precision and (p != "rftc" or KMAX in (8, 10, 12))]
+    order = (others if args.variants == "all" else []) + [args.precision]
     nsample = min(args.cpu_sample_cells, ncells)
     q_sample, invariant_max = {}, {}
     qv = q.view(ncells, KMAX + 1, (LMAX + 1) ** 2)
@@ -829,9 +832,11 @@ def main():
         "roofline": {
             "bound": "alu",
             "pipe": {"fp64": "FP64 FMA (angular coupling + radial contraction)",
-                     "rf32": "FP64 FMA (Gaunt reduction of the radial-first products)"}.get(
+                     "rf32": "FP64 FMA (Gaunt reduction of the radial-first products)",
+                     "rftc": "FP64 FMA (Gaunt reduction of the radial-first products)"}.get(
                          args.precision, "FP64 FMA (angular coupling)"),
-            "kernel": {"fp64": "fp64_kernel", "rf32": f"rf_kernel<{KMAX + 1}>"}.get(
+            "kernel": {"fp64": "fp64_kernel", "rf32": f"rf_kernel<{KMAX + 1}>",
+                       "rftc": f"rft_kernel<{KMAX + 1}>"}.get(
                 args.precision, f"tc_kernel<{KMAX + 1},{args.precision}>"),
             "achieved": achieved,
             "peak": FP64_PEAK_TFLOPS,
@@ -842,7 +847,8 @@ def main():
                             "in + FP64 Q out = 432 MB; " + TRAFFIC_NOTE,
             "fp64_flops_per_cell": head["fp64_flops_per_cell"],
             "radial_flops_per_cell": head["radial_flops_per_cell"],
-            "radial_note": "low-precision radial flops: tensor-core (bf16, tf32) or FP32 CUDA-core (rf32)",
+            "radial_note": "low-precision radial flops: tensor-core (bf16, tf32; rftc: stage 1 as three TF32 "
+                           "products on padded tiles, stage 2 on the FP32 CUDA cores) or FP32 CUDA-core (rf32)",
             "radial_tflops": head["radial_tflops"],
             "kernel_ms": head["kernel_ms"],
             "peak_note": "peak = 152 SMs x 2 DFMA lanes/clock x 2 flop x 2070 MHz; probe = live DFMA chain",

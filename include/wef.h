@@ -57,8 +57,14 @@ typedef enum {
   WEF_FP64 = 0,       /* everything in FP64 (angular coupling and radial contraction) */
   WEF_MIXED_BF16 = 1, /* FP64 angular coupling, BF16 x BF16 -> FP32 radial stage on tcgen05 */
   WEF_MIXED_TF32 = 2, /* FP64 angular coupling, TF32 x TF32 -> FP32 radial stage on tcgen05 */
-  WEF_RADIAL_FP32 = 3 /* radial-first ordering: both radial contractions in FP32 on the CUDA cores,
-                         Gaunt-weighted angular reduction in FP64 (Sec. 4.5.3 made dense) */
+  WEF_RADIAL_FP32 = 3, /* radial-first ordering: both radial contractions in FP32 on the CUDA cores,
+                          Gaunt-weighted angular reduction in FP64 (Sec. 4.5.3 made dense) */
+  WEF_RADIAL_TC = 4    /* radial-first ordering as WEF_RADIAL_FP32, the first radial contraction (the
+                          core, shared by all cells, times f) on tcgen05 in split TF32 (three TF32
+                          products per term, FP32 accumulation); Kmax = 8, 10 or 12.  Taken by the
+                          one-shape calls (wef_workspace_size, wef_evaluate and those built on it:
+                          wef_evaluate_host, wef_integrate, wef_linearized_apply) and wef_flops; plans
+                          and ragged batches refuse it */
 } wef_precision;
 
 /* Flags of wef_upload_core. */
@@ -298,7 +304,10 @@ wef_status wef_core_build_device(wef_op op, int pad_rad, int pad_ang, double* R_
  * coupling, plus the radial contraction for WEF_FP64) and tensor-core flops
  * (radial contraction, padded MMA shapes, for the mixed precisions).  An FMA
  * counts as 2.  For WEF_RADIAL_FP32 the second output is the FP32 CUDA-core work of
- * the two radial contractions instead.  Derived from the operator's programs; any
+ * the two radial contractions instead; for WEF_RADIAL_TC the tensor-core work of the
+ * first radial contraction as executed (three TF32 products per term on tiles padded to
+ * 16 k2 x 16 K columns, the 32 cells of a tile repeated over the four tensor-memory lane
+ * quadrants).  Derived from the operator's programs; any
  * out pointer may be NULL.  Errors: WEF_EINVAL (op NULL, unknown precision).
  */
 wef_status wef_flops(wef_op op, wef_precision prec, double* fp64_flops_per_cell, double* tc_flops_per_cell);

@@ -15,9 +15,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libwef.so")
 
 WEF_OK, WEF_EINVAL, WEF_ENOMEM, WEF_ECUDA, WEF_ENOCORE, WEF_ESHAPE, WEF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-WEF_FP64, WEF_MIXED_BF16, WEF_MIXED_TF32, WEF_RADIAL_FP32 = 0, 1, 2, 3
+WEF_FP64, WEF_MIXED_BF16, WEF_MIXED_TF32, WEF_RADIAL_FP32, WEF_RADIAL_TC = 0, 1, 2, 3, 4
 WEF_CORE_APPLY_NULLSPACE = 1
-PRECISIONS = {"fp64": WEF_FP64, "bf16": WEF_MIXED_BF16, "tf32": WEF_MIXED_TF32, "rf32": WEF_RADIAL_FP32}
+PRECISIONS = {"fp64": WEF_FP64, "bf16": WEF_MIXED_BF16, "tf32": WEF_MIXED_TF32, "rf32": WEF_RADIAL_FP32,
+              "rftc": WEF_RADIAL_TC}
 
 _lib = None
 

@@ -13,7 +13,7 @@ cudaError_t launch_rf_tmem(int K, const float* ftile32, int* queue, double* q, i
   switch (K) {
 #define WEF_RF(k) \
   case k:         \
-    return rfk::launch_rf_k<k, true>(ftile32, queue, q, ncells, NQ, r, R32, nsm, s, ev0, ev1, rv, group_bytes);
+    return rfk::launch_rf_k<k, kRfAccTmem>(ftile32, queue, q, ncells, NQ, r, R32, nsm, s, ev0, ev1, rv, group_bytes);
     WEF_RF(1) WEF_RF(2) WEF_RF(3) WEF_RF(4) WEF_RF(5) WEF_RF(6) WEF_RF(7) WEF_RF(8) WEF_RF(9) WEF_RF(10) WEF_RF(11)
     WEF_RF(12) WEF_RF(13) WEF_RF(14) WEF_RF(15) WEF_RF(16) WEF_RF(17)
 #undef WEF_RF

@@ -31,6 +31,7 @@ struct wef_operator {
   uint8_t* d_Bbf16 = nullptr;   // packed MMA B tiles, BF16
   uint8_t* d_Btf32 = nullptr;   // packed MMA B tiles, TF32
   float* d_R32 = nullptr;       // symmetrised core, FP32 [sc][k1][k2][KP4] (radial-first path)
+  uint8_t* d_Brft = nullptr;    // split-TF32 b tiles of the tensor-core radial-first stage 1
   bool has_core = false;
   // tracing
   cudaEvent_t trace_start = nullptr, trace_stop = nullptr;
@@ -60,7 +61,9 @@ struct wef_operator {
     cudaFree(d_Bbf16);
     cudaFree(d_Btf32);
     cudaFree(d_R32);
+    cudaFree(d_Brft);
     d_R32 = nullptr;
+    d_Brft = nullptr;
     d_R64 = nullptr;
     d_Bbf16 = d_Btf32 = nullptr;
     has_core = false;

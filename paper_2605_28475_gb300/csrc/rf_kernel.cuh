@@ -124,15 +124,16 @@ struct RfCfg {
   static constexpr int MAXREG_1CTA = MAXREG_1CTA_RAW > 255 ? 255 : MAXREG_1CTA_RAW;
 };
 
-template <int K, bool TMEM>
-__global__ void __launch_bounds__(32 * K) __maxnreg__(TMEM ? RfCfg<K>::MAXREG_1CTA : RfCfg<K>::MAXREG)
+template <int K, int ACC>
+__global__ void __launch_bounds__(32 * K) __maxnreg__(ACC == kRfAccTmem ? RfCfg<K>::MAXREG_1CTA : RfCfg<K>::MAXREG)
     rf_kernel(const float* __restrict__ ftile, double* __restrict__ qout, int64_t ncells, int64_t ntiles, int NQ,
               const int4* __restrict__ tasks, const int4* __restrict__ chans, const int4* __restrict__ blocks,
               const int4* __restrict__ uents, const double2* __restrict__ pw,
               const int32_t* __restrict__ order, int ntasks, const float* __restrict__ R32, int* __restrict__ queue,
               int64_t group, int n1max, uint32_t tcols, RaggedView rv) {
   using Cfg = RfCfg<K>;
-  constexpr int J = rf_group_width(K, TMEM), KH = Cfg::KH, R4 = Cfg::KP4 / 4, S = K * 32;
+  constexpr bool TMEM = ACC != kRfAccSmem;
+  constexpr int J = rf_group_width(K, ACC == kRfAccTmem), KH = Cfg::KH, R4 = Cfg::KP4 / 4, S = K * 32;
   __shared__ int item_s;
   const int k1 = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (rv.count) {  // one shape of a ragged batch: its size and tiles come from the device
@@ -276,10 +277,10 @@ __global__ void __launch_bounds__(32 * K) __maxnreg__(TMEM ? RfCfg<K>::MAXREG_1C
 
 // Shared-memory opt-in of one instantiation (so that later launches, possibly under
 // stream capture, make no attribute calls).
-template <int K, bool TMEM>
+template <int K, int ACC>
 cudaError_t prepare_rf_k(size_t smem) {
   static std::atomic<size_t> attr[kMaxDevices];
-  return smem > 0 ? smem_opt_in(rf_kernel<K, TMEM>, smem, attr) : cudaSuccess;
+  return smem > 0 ? smem_opt_in(rf_kernel<K, ACC>, smem, attr) : cudaSuccess;
 }
 
 // Launches the persistent radial-first kernel (the queue was reset and the FP32 tiles
@@ -287,29 +288,31 @@ cudaError_t prepare_rf_k(size_t smem) {
 // ncells: the cells of a one-shape call, or (rv.count set) an upper bound of the shape's
 // cells in a ragged batch, which sizes the grid.
 // group_bytes: FP32 tile bytes per L2 tile group (0: 24 MB).
-template <int K, bool TMEM>
+template <int K, int ACC>
 cudaError_t launch_rf_k(const float* ftile32, int* queue, double* q, int64_t ncells, int NQ, const DevRadial& r,
                         const float* R32, int nsm, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
                         const RaggedView& rv = RaggedView(), int64_t group_bytes = 0) {
   constexpr int threads = 32 * K;
+  constexpr bool TMEM = ACC != kRfAccSmem;
   const int64_t ntiles = (ncells + 31) / 32;
   const size_t smem = TMEM ? 0 : (size_t)r.n1max * threads * sizeof(double);
   uint32_t tcols = 0;
   if (TMEM) {
     // columns: ceil(K / 4) warps share a lane quadrant, 2 columns per FP64 accumulator
-    const uint32_t need = (uint32_t)((K + 3) / 4) * 2u * (uint32_t)r.n1max;
-    tcols = 32;
-    while (tcols < need) tcols <<= 1;
+    tcols = (uint32_t)rf_tmem_cols(K, r.n1max);
     if (tcols > 512) return cudaErrorInvalidValue;
   }
   {
-    cudaError_t e = prepare_rf_k<K, TMEM>(smem);
+    cudaError_t e = prepare_rf_k<K, ACC>(smem);
     if (e != cudaSuccess) return e;
   }
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rf_kernel<K, TMEM>, threads, smem);
-  if (per_sm < 1) per_sm = 1;
-  if (tcols > 0 && per_sm > (int)(512 / tcols)) per_sm = (int)(512 / tcols);  // tensor memory per SM
+  if (TMEM) {
+    per_sm = tmem_ctas_per_sm(rf_kernel<K, ACC>, threads, smem, (int)tcols);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rf_kernel<K, ACC>, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+  }
   const int64_t nitems = ntiles * r.ntasks;
   int64_t grid = (int64_t)nsm * per_sm;
   if (grid > nitems) grid = nitems;
@@ -322,7 +325,7 @@ cudaError_t launch_rf_k(const float* ftile32, int* queue, double* q, int64_t nce
   int64_t group = (group_bytes > 0 ? group_bytes : (24LL << 20)) / tile_bytes;
   if (group < 1) group = 1;
   if (group > ntiles) group = ntiles;
-  rf_kernel<K, TMEM><<<(unsigned)grid, threads, smem, s>>>(ftile32, q, ncells, ntiles, NQ, r.tasks, r.chans, r.blocks,
+  rf_kernel<K, ACC><<<(unsigned)grid, threads, smem, s>>>(ftile32, q, ncells, ntiles, NQ, r.tasks, r.chans, r.blocks,
                                                      r.uents, r.pw, r.order, r.ntasks, R32, queue, group,
                                                      r.n1max, tcols, rv);
   if (ev1) cudaEventRecord(ev1, s);

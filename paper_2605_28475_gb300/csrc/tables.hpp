@@ -51,6 +51,16 @@ struct Program {
 WEF_HD constexpr bool rf_uses_tmem(int K, int n1max) {
   return 2 * ((long long)n1max * 32 * K * 8 + 1024) > 228LL * 1024;
 }
+// Accumulator variants of the radial-first kernel (template argument ACC): shared memory with
+// the register budget of rf_ctas_per_sm(K) CTAs per SM; tensor memory with one CTA per SM
+// (rf_uses_tmem); tensor memory with the register budget of rf_ctas_per_sm(K) CTAs, whose
+// columns (rf_tmem_cols each) fit in the SM's 512.
+constexpr int kRfAccSmem = 0, kRfAccTmem = 1, kRfAccTmem2 = 2;
+WEF_HD constexpr int rf_tmem_cols(int K, int n1max) {
+  int need = (K + 3) / 4 * 2 * n1max, c = 32;
+  while (c < need) c <<= 1;
+  return c;
+}
 // q2 groups the radial-first kernel keeps in registers at once (rf_group_width): its
 // register budget is that of two CTAs per SM with shared-memory accumulators, of one with
 // tensor memory.  Three groups at K = 12-13 (measured at K = 13 with the next union record

@@ -196,9 +196,24 @@ wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigne
         for (int k2 = 0; k2 < K; ++k2)
           for (int k3 = 0; k3 < K; ++k3)
             R32[(((size_t)s * K + k1) * K + k2) * KP4 + k3] = (float)R64[(((size_t)s * K + k3) * K + k1) * K + k2];
+    // split-TF32 b tiles of the tensor-core first radial stage (WEF_RADIAL_TC), per channel
+    std::vector<uint8_t> Brft;
+    if (rft_supported(K)) {
+      const size_t nb = 2 * (size_t)rft_b_tile_bytes(K);
+      Brft.resize((size_t)NS * nb);
+      std::vector<double> Rt((size_t)K3);
+      for (int s = 0; s < NS; ++s) {
+        for (int k1 = 0; k1 < K; ++k1)
+          for (int k2 = 0; k2 < K; ++k2)
+            for (int k3 = 0; k3 < K; ++k3)
+              Rt[((size_t)k1 * K + k2) * K + k3] = R64[(((size_t)s * K + k3) * K + k1) * K + k2];
+        rft_pack_b_tiles(K, Rt.data(), &Brft[(size_t)s * nb]);
+      }
+    }
     op->release_core();
     cudaError_t e = upload(&op->d_R64, R64);
     if (e == cudaSuccess) e = upload(&op->d_R32, R32);
+    if (e == cudaSuccess) e = upload(&op->d_Brft, Brft);
     if (e == cudaSuccess) e = upload(&op->d_Bbf16, Bb);
     if (e == cudaSuccess) e = upload(&op->d_Btf32, Bt);
     if (e != cudaSuccess) {
@@ -212,11 +227,11 @@ wef_status wef_upload_core(wef_op op, const double* R_host, int64_t len, unsigne
 
 wef_status wef_workspace_size(wef_op op, int64_t ncells, wef_precision prec, int64_t* bytes) {
   if (!op || !bytes || ncells < 0) return fail(WEF_EINVAL, "wef_workspace_size: bad argument");
-  if (!valid_precision(prec)) return fail(WEF_EINVAL, "wef_workspace_size: unknown precision");
+  if (!valid_eval_precision(prec)) return fail(WEF_EINVAL, "wef_workspace_size: unknown precision");
   const int64_t ntiles = (ncells + 31) / 32;
   const int64_t tile_elems = ntiles * 32 * (int64_t)op->T.K * op->T.NQ;
   *bytes = tile_elems * (int64_t)sizeof(double);
-  if (prec == WEF_RADIAL_FP32 && ncells > 0) {
+  if (radial_first(prec) && ncells > 0) {
     // queue word (256 bytes) + FP32 re-tiled f
     const int64_t rb = 256 + (tile_elems * (int64_t)sizeof(float) + 255) / 256 * 256;
     if (rb > *bytes) *bytes = rb;
@@ -235,7 +250,9 @@ wef_status wef::evaluate_grouped(wef_op op, const double* f_dev, double* q_dev, 
                                  void* workspace, int64_t workspace_bytes, void* stream, int64_t group_bytes) {
   return wef::guarded("wef_evaluate", [&]() -> wef_status {
     if (!op) return fail(WEF_EINVAL, "wef_evaluate: op is NULL");
-    if (!valid_precision(prec)) return fail(WEF_EINVAL, "wef_evaluate: unknown precision");
+    if (!valid_eval_precision(prec)) return fail(WEF_EINVAL, "wef_evaluate: unknown precision");
+    if (prec == WEF_RADIAL_TC && !rft_supported(op->T.K))
+      return fail(WEF_EINVAL, "wef_evaluate: WEF_RADIAL_TC is compiled for Kmax = 8, 10 and 12 only");
     if (ncells < 0) return fail(WEF_EINVAL, "wef_evaluate: ncells < 0");
     if (ncells == 0) return WEF_OK;
     if (!f_dev || !q_dev || !workspace) return fail(WEF_EINVAL, "wef_evaluate: NULL buffer");
@@ -260,6 +277,16 @@ wef_status wef::evaluate_grouped(wef_op op, const double* f_dev, double* q_dev, 
       cudaError_t er = launch_rf(K, f_dev, (float*)((char*)workspace + 256), (int*)workspace, q_dev, ncells, NQ, r,
                                  op->d_R32, op->sms, s, op->trace_start, op->trace_stop, group_bytes);
       if (er != cudaSuccess) return cuda_fail(er, "wef_evaluate: radial-first kernels");
+      return WEF_OK;
+    }
+    if (prec == WEF_RADIAL_TC) {
+      const RadialProgram& RP = op->T.rprog;
+      DevRadial r{(const int4*)op->r_tasks, (const int4*)op->r_chans, (const int4*)op->r_blocks,
+                  (const int4*)op->r_uents, (const double2*)op->r_pw, op->r_order,
+                  (int)RP.task_cost.size(), RP.n1max};
+      cudaError_t er = launch_rft(K, f_dev, (float*)((char*)workspace + 256), (int*)workspace, q_dev, ncells, NQ, r,
+                                  op->d_Brft, op->sms, op->d_status, s, op->trace_start, op->trace_stop, group_bytes);
+      if (er != cudaSuccess) return cuda_fail(er, "wef_evaluate: radial-first tensor-core kernels");
       return WEF_OK;
     }
     double* ftile = (double*)workspace;
@@ -302,10 +329,18 @@ wef_status wef_core_build(wef_op op, int pad_rad, int pad_ang, double* R_out, in
 
 wef_status wef_flops(wef_op op, wef_precision prec, double* fp64_flops_per_cell, double* tc_flops_per_cell) {
   if (!op) return fail(WEF_EINVAL, "wef_flops: op is NULL");
-  if (!valid_precision(prec)) return fail(WEF_EINVAL, "wef_flops: unknown precision");
+  if (!valid_eval_precision(prec)) return fail(WEF_EINVAL, "wef_flops: unknown precision");
   if (prec == WEF_RADIAL_FP32) {
     if (fp64_flops_per_cell) *fp64_flops_per_cell = op->T.rprog.fp64_flops;
     if (tc_flops_per_cell) *tc_flops_per_cell = op->T.rprog.fp32_flops;
+    return WEF_OK;
+  }
+  if (prec == WEF_RADIAL_TC) {
+    // tensor-core stage 1 as executed: per q2 group, three TF32 products of a 128-row tile
+    // (the 32 cells four times) by 16 k2 by 16 K columns, i.e. per cell 4 x 3 x 2 x 16 x 16 K
+    const int K = op->T.K;
+    if (fp64_flops_per_cell) *fp64_flops_per_cell = op->T.rprog.fp64_flops;
+    if (tc_flops_per_cell) *tc_flops_per_cell = (double)op->T.rprog.n_groups * 4.0 * 3.0 * 2.0 * 16.0 * 16.0 * K;
     return WEF_OK;
   }
   const Program& P = prec == WEF_FP64 ? op->T.prog1 : op->T.prog4;

@@ -10,6 +10,7 @@
 #include "tables.hpp"
 #include "../../include/wef.h"
 
+#include <algorithm>
 #include <atomic>
 
 namespace wef {
@@ -18,6 +19,10 @@ namespace wef {
 inline bool valid_precision(wef_precision p) {
   return p == WEF_FP64 || p == WEF_MIXED_BF16 || p == WEF_MIXED_TF32 || p == WEF_RADIAL_FP32;
 }
+// The precisions of the one-shape evaluation (wef_evaluate and the calls built on it).
+inline bool valid_eval_precision(wef_precision p) { return valid_precision(p) || p == WEF_RADIAL_TC; }
+// Radial-first precisions: FP32 re-tiled f and a queue word in the workspace.
+inline bool radial_first(wef_precision p) { return p == WEF_RADIAL_FP32 || p == WEF_RADIAL_TC; }
 
 // Device copy of one Program (see tables.hpp).
 struct DevProgram {
@@ -73,6 +78,30 @@ cudaError_t smem_opt_in(Fn fn, size_t bytes, std::atomic<size_t>* done) {
   return e;
 }
 
+// CTAs per SM of a kernel that allocates `tcols` tensor-memory columns per CTA, from its
+// registers, shared memory and threads and the SM's 512 columns.  (The runtime's occupancy
+// query answers 1 for every kernel that uses tcgen05.alloc, whatever its resources; the
+// allocation itself only waits while the SM's columns are taken.)
+template <class Fn>
+int tmem_ctas_per_sm(Fn fn, int threads, size_t dyn_smem, int tcols) {
+  int dev = 0, regs_sm = 0, smem_sm = 0, reserved = 0, thr_sm = 0, blk_sm = 0;
+  cudaFuncAttributes a{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&a, fn) != cudaSuccess) return 1;
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+  const int warps = (threads + 31) / 32;
+  const long long regs_warp = ((long long)a.numRegs * 32 + 255) / 256 * 256;  // allocated per warp
+  long long n = tcols > 0 ? 512 / tcols : blk_sm;
+  if (regs_warp > 0) n = std::min(n, (long long)regs_sm / (regs_warp * warps));
+  n = std::min(n, (long long)smem_sm / (long long)(a.sharedSizeBytes + dyn_smem + reserved));
+  n = std::min(n, (long long)thr_sm / (warps * 32));
+  if (blk_sm > 0) n = std::min(n, (long long)blk_sm);
+  return n < 1 ? 1 : (int)n;
+}
+
 // Releases the cuBLAS handle of the dense baseline.
 void destroy_cublas(void* handle);
 
@@ -112,6 +141,18 @@ cudaError_t launch_fp64(int K, const double* ftile, double* q, int64_t ncells, i
                         const RaggedView& rv = RaggedView());
 
 // Tensor-core path: bytes of one packed core tile (MMA B operand) and its packing.
+// Radial-first evaluation with the first radial stage on the tensor cores
+// (WEF_RADIAL_TC, kernels_rft.cu).  One symmetrised channel's MMA b operand is two tiles
+// (TF32 hi, then lo) of 16 K rows n = 16 k1 + k3 by 16 k2, K-major core matrices.
+WEF_HD constexpr int rft_b_tile_bytes(int K) { return 16 * K * 16 * 4; }
+// Radial-function counts with a compiled kernel (the TF32 split of stage 1 needs a 16 K + 32
+// column tensor-memory tile per CTA, two CTAs per SM).
+inline bool rft_supported(int K) { return K == 9 || K == 11 || K == 13; }
+void rft_pack_b_tiles(int K, const double* Rt /* [k1][k2][k3] */, uint8_t* out /* 2 rft_b_tile_bytes(K) */);
+cudaError_t launch_rft(int K, const double* f, float* ftile32, int* queue, double* q, int64_t ncells, int NQ,
+                       const DevRadial& r, const uint8_t* Bt, int nsm, int* status, cudaStream_t s, cudaEvent_t ev0,
+                       cudaEvent_t ev1, int64_t group_bytes);
+cudaError_t launch_tile_f32(const double* f, float* ftile32, int64_t ncells, int K, int NQ, cudaStream_t s);
 int tc_b_tile_bytes(int K, bool tf32);
 void tc_pack_b_tile(int K, bool tf32, const double* Rt /* [k1][k2][k3] */, uint8_t* out);
 

@@ -97,6 +97,18 @@ def test_argument_errors():
         with pytest.raises(W.WefError) as e:
             W.wef_evaluate(h, 0, 0, 0, 7, 0, 0, 0)
         assert e.value.status == W.WEF_EINVAL and "precision" in str(e.value)
+        # the tensor-core radial-first path exists for Kmax = 8, 10, 12 only (here Kmax = 2),
+        # and is a one-shape path: plans and ragged batches refuse it
+        with pytest.raises(W.WefError) as e:
+            W.wef_evaluate(h, 0, 0, 1, W.WEF_RADIAL_TC, 0, 0, 0)
+        assert e.value.status == W.WEF_EINVAL and "Kmax" in str(e.value)
+        assert W.wef_workspace_size(h, 33, W.WEF_RADIAL_TC) == W.wef_workspace_size(h, 33, W.WEF_RADIAL_FP32)
+        with pytest.raises(W.WefError) as e:
+            W.wef_plan_create([h], [32], W.WEF_RADIAL_TC, 0)
+        assert e.value.status == W.WEF_EINVAL
+        with pytest.raises(W.WefError) as e:
+            W.wef_ragged_workspace_size([h], 32, W.WEF_RADIAL_TC)
+        assert e.value.status == W.WEF_EINVAL
     finally:
         W.wef_destroy(h)
 
@@ -147,11 +159,15 @@ def test_flop_counts_match_the_coo_table(km, lm):
     h = W.wef_create(km, lm, 1.0)
     try:
         fp64, fp32 = W.wef_flops(h, W.WEF_RADIAL_FP32)
+        tc64, tc = W.wef_flops(h, W.WEF_RADIAL_TC)
         plain, _ = W.wef_flops(h, W.WEF_FP64)
     finally:
         W.wef_destroy(h)
     assert fp64 == 2 * K * E
     assert fp32 == 2 * K**3 * len(groups) + 2 * K**2 * len(pairs)
+    # tensor-core stage 1 as executed: per (channel, q2) group three TF32 products of the
+    # 32 cells repeated over the 4 lane quadrants by 16 (padded k2) by 16 K (k1, padded k3)
+    assert tc64 == fp64 and tc == len(groups) * 4 * 3 * 2 * 16 * 16 * K
     assert plain == 2 * K**2 * len(rank1) + 2 * K * E + 2 * K**3 * len(slices)
 
 

@@ -182,6 +182,37 @@ def test_radial_first_random_core(km, lm, ncells):
     _check(Q, _oracle(km, lm, R, f), "rf32", f"random core K={km + 1} L={lm} n={ncells}")
 
 
+# radial-first with the first radial stage on the tcgen05 tensor cores (split TF32): the
+# radial-function counts it is compiled for, ragged tails, a shell wider than the program's
+# q2 blocks (Lmax = 16), and agreement with the CUDA-core radial-first path
+@pytest.mark.parametrize("km,lm,ncells", [(8, 8, 37), (10, 10, 45), (12, 12, 33), (12, 4, 70), (8, 3, 5)])
+def test_radial_first_tensor_core_stage1(km, lm, ncells):
+    nt = len(gaunt.channels(lm))
+    R = wi.random_core(nt, km, seed=km * 100 + lm + 9)
+    f = wi.random_cells(km, lm, ncells, seed=lm + 9)
+    op = W.Operator(km, lm, 0.0)
+    op.upload_core(R)
+    Q = _gpu_eval(op, f, "rftc")
+    W.wef_device_status(op.h)  # no bounded wait gave up
+    _check(Q, _oracle(km, lm, R, f), "rftc", f"random core K={km + 1} L={lm} n={ncells}")
+    assert np.all(Q[:, 0, 0:4] == 0.0) and np.all(Q[:, 1, 0] == 0.0)
+    assert np.array_equal(Q, _gpu_eval(op, f, "rftc"))  # deterministic
+    d = np.abs(Q - _gpu_eval(op, f, "rf32")).max() / np.abs(Q).max()
+    assert d < 2.0 ** -20, d  # both paths are FP32-accurate in the radial products
+
+
+def test_radial_first_tensor_core_wide_shell():
+    """Kmax = 12 with Lmax = 16: the largest shells' accumulators (33 q1) take one CTA per SM."""
+    km, lm, ncells = 12, 16, 3
+    R = wi.random_core(len(gaunt.channels(lm)), km, seed=31)
+    f = wi.random_cells(km, lm, ncells, seed=32)
+    op = W.Operator(km, lm, 0.0)
+    op.upload_core(R)
+    Q = _gpu_eval(op, f, "rftc").reshape(ncells, -1)
+    rows = sorted(set([0, 1, 2, 3, op.NQ, op.N - 1] + list(np.random.default_rng(2).choice(op.N, 10, replace=False))))
+    _check(Q[:, rows], _oracle(km, lm, R, f, rows), "rftc", "K=13 L=16 sampled rows")
+
+
 def test_radial_first_invariants_and_rerun():
     km, lm = 4, 4
     R = wi.random_core(len(gaunt.channels(lm)), km, seed=3)
@@ -226,7 +257,7 @@ def kl12_random():
 
 
 @pytest.mark.parametrize("core", ["kl12_hs", "kl12_random"])
-@pytest.mark.parametrize("prec", ["fp64", "bf16", "tf32", "rf32"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16", "tf32", "rf32", "rftc"])
 def test_full_size_kl12_sampled(request, core, prec):
     km, lm, R, f, idx, oracle = request.getfixturevalue(core)
     op = W.Operator(km, lm, 1.0)
