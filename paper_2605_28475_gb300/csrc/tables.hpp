@@ -46,10 +46,13 @@ struct Program {
 #define WEF_HD
 #endif
 
-// Whether the radial-first kernel keeps the FP64 accumulators of the largest shell (n1max
-// targets) in tensor memory: when two CTAs' worth do not fit in an SM's shared memory.
+// Whether the radial-first kernel runs one CTA per SM with the whole register file (and its
+// FP64 accumulators in tensor memory): from K = 15 on, where the register budget of two CTAs
+// leaves room for one q2 group per block only (K = 17, Lmax = 8-12: 0.30-0.37 of the FP64
+// peak with two CTAs), and wherever two CTAs' accumulators (largest shell, n1max targets)
+// would not fit in an SM's shared memory.
 WEF_HD constexpr bool rf_uses_tmem(int K, int n1max) {
-  return 2 * ((long long)n1max * 32 * K * 8 + 1024) > 228LL * 1024;
+  return K >= 15 || 2 * ((long long)n1max * 32 * K * 8 + 1024) > 228LL * 1024;
 }
 // Accumulator variants of the radial-first kernel (template argument ACC): shared memory with
 // the register budget of rf_ctas_per_sm(K) CTAs per SM; tensor memory with one CTA per SM
@@ -62,8 +65,8 @@ WEF_HD constexpr int rf_tmem_cols(int K, int n1max) {
   return c;
 }
 // q2 groups the radial-first kernel keeps in registers at once (rf_group_width): its
-// register budget is that of two CTAs per SM with shared-memory accumulators, of one with
-// tensor memory.  Three groups at K = 12-13 (measured at K = 13 with the next union record
+// register budget is that of two CTAs per SM, or of one (rf_uses_tmem).  Three groups at
+// K = 12-14 (K = 14 keeps as many k3 pairs as K = 13) (measured at K = 13 with the next union record
 // prefetched: 379.7k against 343.2k cells/s with two) and with tensor memory above K = 9
 // (K = 17: 56.9k against 49.1k); four overflow the registers there.
 // CTAs per SM the shared-memory variant's register budget is sized for: about 32-36
@@ -73,7 +76,7 @@ WEF_HD constexpr int rf_ctas_per_sm(int K) {
   return K <= 4 ? 8 : K == 5 ? 7 : K == 6 ? 6 : K == 7 ? 5 : K <= 9 ? 4 : 2;
 }
 WEF_HD constexpr int rf_group_width(int K, bool tmem) {
-  return tmem ? (K <= 9 ? 4 : 3) : (K <= 4 ? 4 : K <= 11 ? 2 : K <= 13 ? 3 : 1);
+  return tmem ? (K <= 9 ? 4 : 3) : (K <= 4 ? 4 : K <= 11 ? 2 : K <= 14 ? 3 : 1);
 }
 
 // Radial-first program (paper Sec. 4.5.3 ordering with a dense two-stage radial
