@@ -329,79 +329,82 @@ std::string core_build(const Tables& T, double gamma, int pad_rad, int pad_ang, 
       for (int i = 0; i < Nx1; ++i) items.push_back({iz, i, 1, half});
       for (int i = 0; i < Ny2; ++i) items.push_back({iz, i, 2, half});
     }
-  unsigned nth = std::max(1u, std::thread::hardware_concurrency());
-  std::vector<std::vector<double>> acc(nth);
-  std::atomic<size_t> next(0);
+  // Deterministic reduction: item i is added, in item order, into partial sum i % kParts,
+  // and the partial sums are added in a fixed order, so the core is bitwise the same for any
+  // thread count and schedule (replicas built by ranks on the same kind of host agree exactly).
+  constexpr unsigned kParts = 16;
+  const unsigned nth = std::min(kParts, std::max(1u, std::thread::hardware_concurrency()));
+  std::vector<std::vector<double>> acc(kParts);
   const double pref = C.pref;
   auto worker = [&](unsigned tid) {
-    std::vector<double>& Racc = acc[tid];
-    Racc.assign(RL, 0.0);
     const int nbuf = 2 * L1 * L1 + 3 * K * L1;
     std::vector<double> buf(nbuf), A((size_t)NT * K), Abar((size_t)NT * K), Rv(K * L1), Rw(K * L1);
     const int maxh = std::max(Nh1, Nh2);
     std::vector<double> Ap((size_t)maxh * NT * K), Rvp((size_t)maxh * K * L1), Rwp((size_t)maxh * K * L1);
-    for (;;) {
-      const size_t it = next.fetch_add(1);
-      if (it >= items.size()) break;
-      const Item& I = items[it];
-      const double z = zz[I.iz], sz = std::sqrt(z);
-      const double sgn = I.half == 0 ? 1.0 : -1.0;
-      if (I.patch == 1) {
-        // outer x, inner h: y = x h; v, w fixed over the inner loop
-        const double xa = rx1.x[I.io], x = sgn * xa;
-        const double v = sz * (1.0 + x), w = sz * (1.0 - x);
-        std::fill(Abar.begin(), Abar.end(), 0.0);
-        for (int ih = 0; ih < Nh1; ++ih) {
-          const double h = rh1.x[ih], y = xa * h;
-          const double sing = std::pow(xa, gamma) * std::pow(1.0 + (1.0 - xa * xa) * h * h, 0.5 * gamma);
-          const double W = wz[I.iz] * rx1.w[I.io] * rh1.w[ih] * xa * sing * std::exp(-z * xa * xa) * z * z *
-                           (1.0 - xa * xa) * (1.0 - xa * xa) * y * pref;
-          channel_terms(C, v, w, 1.0 - 2.0 * y * y, y, A.data(), buf.data());
-          for (size_t j = 0; j < A.size(); ++j) Abar[j] += W * A[j];
-        }
-        radial_all(C, v, Rv.data());
-        radial_all(C, w, Rw.data());
-        for (int c = 0; c < NT; ++c) {
-          const Channel& h = C.ch[c];
-          double* Rc = &Racc[(size_t)c * K * K * K];
-          for (int k1 = 0; k1 < K; ++k1) {
-            const double a = Abar[c * K + k1];
-            for (int k2 = 0; k2 < K; ++k2) {
-              const double ab = a * Rv[k2 * L1 + h.l2];
-              double* row = Rc + ((size_t)k1 * K + k2) * K;
-              for (int k3 = 0; k3 < K; ++k3) row[k3] += ab * Rw[k3 * L1 + h.l3];
+    for (unsigned part = tid; part < kParts; part += nth) {
+      std::vector<double>& Racc = acc[part];
+      Racc.assign(RL, 0.0);
+      for (size_t it = part; it < items.size(); it += kParts) {
+        const Item& I = items[it];
+        const double z = zz[I.iz], sz = std::sqrt(z);
+        const double sgn = I.half == 0 ? 1.0 : -1.0;
+        if (I.patch == 1) {
+          // outer x, inner h: y = x h; v, w fixed over the inner loop
+          const double xa = rx1.x[I.io], x = sgn * xa;
+          const double v = sz * (1.0 + x), w = sz * (1.0 - x);
+          std::fill(Abar.begin(), Abar.end(), 0.0);
+          for (int ih = 0; ih < Nh1; ++ih) {
+            const double h = rh1.x[ih], y = xa * h;
+            const double sing = std::pow(xa, gamma) * std::pow(1.0 + (1.0 - xa * xa) * h * h, 0.5 * gamma);
+            const double W = wz[I.iz] * rx1.w[I.io] * rh1.w[ih] * xa * sing * std::exp(-z * xa * xa) * z * z *
+                             (1.0 - xa * xa) * (1.0 - xa * xa) * y * pref;
+            channel_terms(C, v, w, 1.0 - 2.0 * y * y, y, A.data(), buf.data());
+            for (size_t j = 0; j < A.size(); ++j) Abar[j] += W * A[j];
+          }
+          radial_all(C, v, Rv.data());
+          radial_all(C, w, Rw.data());
+          for (int c = 0; c < NT; ++c) {
+            const Channel& h = C.ch[c];
+            double* Rc = &Racc[(size_t)c * K * K * K];
+            for (int k1 = 0; k1 < K; ++k1) {
+              const double a = Abar[c * K + k1];
+              for (int k2 = 0; k2 < K; ++k2) {
+                const double ab = a * Rv[k2 * L1 + h.l2];
+                double* row = Rc + ((size_t)k1 * K + k2) * K;
+                for (int k3 = 0; k3 < K; ++k3) row[k3] += ab * Rw[k3 * L1 + h.l3];
+              }
             }
           }
-        }
-      } else {
-        // outer y, inner h: x = y h; v, w change with h
-        const double y = ry2.x[I.io];
-        for (int ih = 0; ih < Nh2; ++ih) {
-          const double h = rh2.x[ih], xa = y * h, x = sgn * xa;
-          const double v = sz * (1.0 + x), w = sz * (1.0 - x);
-          const double sing = std::pow(y, gamma) * std::pow(1.0 + (1.0 - y * y) * h * h, 0.5 * gamma);
-          const double W = wz[I.iz] * ry2.w[I.io] * rh2.w[ih] * y * sing * std::exp(-z * xa * xa) * z * z *
-                           (1.0 - xa * xa) * (1.0 - xa * xa) * y * pref;
-          channel_terms(C, v, w, 1.0 - 2.0 * y * y, y, &Ap[(size_t)ih * NT * K], buf.data());
-          for (size_t j = 0; j < (size_t)NT * K; ++j) Ap[(size_t)ih * NT * K + j] *= W;
-          radial_all(C, v, &Rvp[(size_t)ih * K * L1]);
-          radial_all(C, w, &Rwp[(size_t)ih * K * L1]);
-        }
-        for (int c = 0; c < NT; ++c) {
-          const Channel& hc = C.ch[c];
-          double* Rc = &Racc[(size_t)c * K * K * K];
+        } else {
+          // outer y, inner h: x = y h; v, w change with h
+          const double y = ry2.x[I.io];
           for (int ih = 0; ih < Nh2; ++ih) {
-            const double* a = &Ap[(size_t)ih * NT * K + (size_t)c * K];
-            const double* rv = &Rvp[(size_t)ih * K * L1];
-            const double* rw = &Rwp[(size_t)ih * K * L1];
-            double wl3[32];
-            for (int k3 = 0; k3 < K; ++k3) wl3[k3] = rw[k3 * L1 + hc.l3];
-            for (int k1 = 0; k1 < K; ++k1) {
-              const double a1 = a[k1];
-              for (int k2 = 0; k2 < K; ++k2) {
-                const double ab = a1 * rv[k2 * L1 + hc.l2];
-                double* row = Rc + ((size_t)k1 * K + k2) * K;
-                for (int k3 = 0; k3 < K; ++k3) row[k3] += ab * wl3[k3];
+            const double h = rh2.x[ih], xa = y * h, x = sgn * xa;
+            const double v = sz * (1.0 + x), w = sz * (1.0 - x);
+            const double sing = std::pow(y, gamma) * std::pow(1.0 + (1.0 - y * y) * h * h, 0.5 * gamma);
+            const double W = wz[I.iz] * ry2.w[I.io] * rh2.w[ih] * y * sing * std::exp(-z * xa * xa) * z * z *
+                             (1.0 - xa * xa) * (1.0 - xa * xa) * y * pref;
+            channel_terms(C, v, w, 1.0 - 2.0 * y * y, y, &Ap[(size_t)ih * NT * K], buf.data());
+            for (size_t j = 0; j < (size_t)NT * K; ++j) Ap[(size_t)ih * NT * K + j] *= W;
+            radial_all(C, v, &Rvp[(size_t)ih * K * L1]);
+            radial_all(C, w, &Rwp[(size_t)ih * K * L1]);
+          }
+          for (int c = 0; c < NT; ++c) {
+            const Channel& hc = C.ch[c];
+            double* Rc = &Racc[(size_t)c * K * K * K];
+            for (int ih = 0; ih < Nh2; ++ih) {
+              const double* a = &Ap[(size_t)ih * NT * K + (size_t)c * K];
+              const double* rv = &Rvp[(size_t)ih * K * L1];
+              const double* rw = &Rwp[(size_t)ih * K * L1];
+              double wl3[32];
+              for (int k3 = 0; k3 < K; ++k3) wl3[k3] = rw[k3 * L1 + hc.l3];
+              for (int k1 = 0; k1 < K; ++k1) {
+                const double a1 = a[k1];
+                for (int k2 = 0; k2 < K; ++k2) {
+                  const double ab = a1 * rv[k2 * L1 + hc.l2];
+                  double* row = Rc + ((size_t)k1 * K + k2) * K;
+                  for (int k3 = 0; k3 < K; ++k3) row[k3] += ab * wl3[k3];
+                }
               }
             }
           }
@@ -414,7 +417,7 @@ std::string core_build(const Tables& T, double gamma, int pad_rad, int pad_ang, 
   for (auto& t : th) t.join();
   for (size_t j = 0; j < RL; ++j) {
     double s = 0.0;
-    for (unsigned t = 0; t < nth; ++t) s += acc[t][j];
+    for (unsigned t = 0; t < kParts; ++t) s += acc[t][j];
     R[j] = s;
   }
   for (int c = 0; c < NT; ++c) {
