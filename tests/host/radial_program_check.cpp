@@ -13,6 +13,7 @@ int main() {
   std::vector<std::pair<int, int>> shapes;
   for (int L : {0, 1, 2, 3, 4, 6, 8, 12}) for (int km : {0, 1, 4, 8, 12, 16}) shapes.push_back({L, km});
   for (int L : {16, 20}) shapes.push_back({L, 16});
+  for (int L : {4, 8, 12}) for (int km : {13, 14, 15}) shapes.push_back({L, km});  // K = 14-16
   for (const auto& sh : shapes) {
     const int L = sh.first, km = sh.second;
     Tables T; std::string e = build_tables(km, L, T); if (!e.empty()) { printf("err %s\n", e.c_str()); return 1; }
