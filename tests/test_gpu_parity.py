@@ -171,10 +171,11 @@ def test_mixed_invariants_exact(prec):
 
 # ------------------------------------------------------------------ radial-first (FP32 radial, FP64 angular)
 # (13, 6): K = 14 with three q2 groups at two CTAs per SM; (14, 8) and (15, 12): one CTA per SM
-# from K = 15 on at small Lmax
+# from K = 15 on at small Lmax; (6, 12): shared-memory accumulators (the columns of K = 7 at
+# Lmax = 12 do not fit five CTAs' shares of tensor memory)
 @pytest.mark.parametrize("km,lm,ncells", [(0, 0, 3), (1, 2, 1), (2, 3, 70), (4, 4, 33), (4, 6, 40), (8, 8, 37),
                                           (16, 2, 45), (12, 12, 3), (16, 16, 2), (13, 6, 29), (14, 8, 33),
-                                          (15, 12, 5)])
+                                          (15, 12, 5), (6, 12, 17)])
 def test_radial_first_random_core(km, lm, ncells):
     nt = len(gaunt.channels(lm))
     R = wi.random_core(nt, km, seed=km * 100 + lm + 2)
