@@ -1,7 +1,8 @@
 // Radial-first contraction kernel (the paper's Sec. 4.5.3 ordering: both radial stages
 // first, then the Gaunt reduction of Sec. 4.1-4.2 and the Sec. 4.4 projection), shared by
-// the two translation units that instantiate it with the FP64 accumulators in shared
-// memory or in tensor memory (see kernels_rf.cu).
+// the translation units that instantiate it with the FP64 accumulators in shared memory
+// (kernels_rf.cu, which also holds the dispatch), in tensor memory with several CTAs per SM
+// (kernels_rf_tmem2.cu) and in tensor memory with one CTA per SM (kernels_rf_tmem.cu).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -107,8 +108,8 @@ template <int K>
 struct RfCfg {
   static constexpr int KH = (K + 1) / 2;      // k3 pairs
   static constexpr int KP4 = (K + 3) / 4 * 4;  // padded k3 (float4 core rows)
-  // packed FP32x2 FMAs up to K = 13; two scalar FMAs above, where the tensor-memory
-  // variant runs (measured at K = 17: 60.9k against 59.2k cells/s with packed ones)
+  // packed FP32x2 FMAs up to K = 13; two scalar FMAs above (measured at K = 17, one CTA per
+  // SM: 60.9k against 59.2k cells/s with packed ones)
   static constexpr bool PACKED = K <= 13;
   static constexpr int J = rf_group_width(K, false);  // q2 groups per block, shared-memory variant
   // CTAs per SM the register budget is sized for: about 32-36 resident warps where the
@@ -118,8 +119,8 @@ struct RfCfg {
   static constexpr int WARPS_PER_SMSP = (CTAS * K + 3) / 4;
   static constexpr int MAXREG_RAW = 16384 / (32 * WARPS_PER_SMSP) / 8 * 8;
   static constexpr int MAXREG = MAXREG_RAW > 255 ? 255 : MAXREG_RAW;
-  // The tensor-memory variant runs where the accumulators need more than half of an SM's
-  // 512 columns, i.e. one CTA per SM: it may use the whole register file.
+  // The one-CTA-per-SM variant (rf_uses_tmem: K >= 15, or accumulators too large for two
+  // CTAs) may use the whole register file.
   static constexpr int MAXREG_1CTA_RAW = 16384 / (32 * ((K + 3) / 4)) / 8 * 8;
   static constexpr int MAXREG_1CTA = MAXREG_1CTA_RAW > 255 ? 255 : MAXREG_1CTA_RAW;
 };
