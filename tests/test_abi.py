@@ -187,3 +187,21 @@ def test_plain_c_client(tmp_path):
                     f"-Wl,-rpath,{libdir}", "-Wl,--allow-shlib-undefined"], check=True)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+
+
+def test_tensor_core_stage1_b_tiles(tmp_path):
+    """The split-TF32 core tiles of the tensor-core first radial stage (WEF_RADIAL_TC), as the
+    library packs them at core upload: layout, TF32 exactness, hi + lo = R to 2^-22, padding
+    (tests/host/rft_pack_check.cpp, linked against libwef.so; host code only)."""
+    import shutil
+    import subprocess
+
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no C++ compiler")
+    libdir = os.path.dirname(W.LIB_PATH)
+    exe = str(tmp_path / "rft_pack_check")
+    subprocess.run([gxx, "-O2", "-std=c++17", "-o", exe, os.path.join(ROOT, "tests", "host", "rft_pack_check.cpp"),
+                    f"-L{libdir}", "-lwef", f"-Wl,-rpath,{libdir}", "-Wl,--allow-shlib-undefined"], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "bad=0" in r.stdout, r.stdout + r.stderr
